@@ -1,0 +1,97 @@
+"""Pins of the oracle's lineshapes and barrier factors (building blocks of
+Sec. 3) against closed forms and limits fixed by the mathematics."""
+import math
+
+import pytest
+import torch
+
+from oracle import tdamp
+
+F64 = torch.float64
+M_K, M_PI = 0.493677, 0.13957
+
+
+def _res(shape, m0, g0, L=1, dm=(M_K, M_PI)):
+    return tdamp.Resonance("R", m0, g0, shape, L, dm)
+
+
+@pytest.mark.parametrize("shape,m0,g0,L,dm", [
+    ("MDW", 0.89555, 0.0473, 1, (M_K, M_PI)),
+    ("MDW", 0.77526, 0.1491, 1, (M_PI, M_PI)),
+    ("MDW", 0.78266, 0.00868, 1, (M_PI, M_PI)),
+    ("MDW", 1.27, 0.185, 2, (M_PI, M_PI)),
+    ("CONST", 1.230, 0.420, 0, (0, 0)),
+])
+def test_bw_pole_modulus_and_phase(shape, m0, g0, L, dm):
+    """At s = m0^2 the amplitude is i / (m0 Gamma0): modulus 1/(m0 Gamma0), phase +pi/2."""
+    bw = tdamp.breit_wigner(torch.tensor([m0 * m0], dtype=F64), m0, g0, _res(shape, m0, g0, L, dm), 1.5)[0]
+    assert abs(abs(bw) - 1.0 / (m0 * g0)) <= 1e-13 / (m0 * g0)
+    assert abs(math.atan2(bw.imag, bw.real) - math.pi / 2) < 1e-13
+
+
+def test_mdw_width_at_pole_and_threshold_power():
+    """Gamma(m0^2) = Gamma0; near threshold Gamma(s) ~ q^(2L+1)."""
+    for L, dm in ((1, (M_K, M_PI)), (2, (M_PI, M_PI))):
+        m0, g0 = 0.9, 0.05
+        assert abs(float(tdamp.mass_dependent_width(torch.tensor(m0 * m0, dtype=F64), torch.tensor(m0, dtype=F64),
+                                                    torch.tensor(g0, dtype=F64), L, *dm, 1.5)) - g0) < 1e-16
+        thr = (dm[0] + dm[1]) ** 2
+        # q^2 is linear in (s - thr) near threshold, so Gamma ~ (s - thr)^((2L+1)/2)
+        s1 = torch.tensor(thr * (1 + 1e-7), dtype=F64)
+        s2 = torch.tensor(thr * (1 + 4e-7), dtype=F64)
+        g1 = tdamp.mass_dependent_width(s1, torch.tensor(m0, dtype=F64), torch.tensor(g0, dtype=F64), L, *dm, 1.5)
+        g2 = tdamp.mass_dependent_width(s2, torch.tensor(m0, dtype=F64), torch.tensor(g0, dtype=F64), L, *dm, 1.5)
+        assert abs(float(g2 / g1) / 4 ** ((2 * L + 1) / 2) - 1) < 1e-5
+
+
+def test_const_width_half_maximum_points():
+    """For a constant width |BW|^2 falls to half its peak at s = m0^2 +- m0 Gamma0."""
+    m0, g0 = 1.23, 0.42
+    r = _res("CONST", m0, g0, 0)
+    s = torch.tensor([m0 * m0, m0 * m0 - m0 * g0, m0 * m0 + m0 * g0], dtype=F64)
+    bw2 = tdamp.breit_wigner(s, m0, g0, r, 1.5).abs() ** 2
+    assert abs(float(bw2[1] / bw2[0]) - 0.5) < 1e-14
+    assert abs(float(bw2[2] / bw2[0]) - 0.5) < 1e-14
+
+
+def test_bw_far_from_pole():
+    """Far from the pole |BW| -> 1/|m0^2 - s| up to O(m0 Gamma / |m0^2 - s|)."""
+    m0, g0 = 0.77526, 0.1491
+    r = _res("MDW", m0, g0, 1, (M_PI, M_PI))
+    s = torch.tensor([0.1, 3.0], dtype=F64)
+    bw = tdamp.breit_wigner(s, m0, g0, r, 1.5)
+    rel = (bw.abs() * (m0 * m0 - s).abs() - 1).abs()
+    gam = tdamp.mass_dependent_width(s, torch.tensor(m0, dtype=F64), torch.tensor(g0, dtype=F64), 1, M_PI, M_PI, 1.5)
+    assert torch.all(rel <= (m0 * gam / (m0 * m0 - s).abs()) ** 2)
+
+
+def test_blatt_weisskopf_limits():
+    z0 = torch.tensor([0.0], dtype=F64)
+    assert float(tdamp.blatt_weisskopf(0, z0, 1.0)) == 1.0
+    assert float(tdamp.blatt_weisskopf(1, z0, 1.0)) == 1.0
+    assert abs(float(tdamp.blatt_weisskopf(2, z0, 1.0)) - 1.0 / 3.0) < 1e-16
+    big = torch.tensor([1e12], dtype=F64)
+    assert abs(float(tdamp.blatt_weisskopf(1, big, 1.0) * big.sqrt()) - 1) < 1e-6
+    assert abs(float(tdamp.blatt_weisskopf(2, big, 1.0) * big) - 1) < 1e-5
+
+
+def test_blatt_weisskopf_matches_von_hippel_quigg_ratio():
+    """z^(L/2) F_L(z) is proportional to the von Hippel-Quigg barrier factor
+    B_1 = sqrt(2z/(1+z)), B_2 = sqrt(13 z^2 / (9 + 3z + z^2))."""
+    q2 = torch.tensor([0.01, 0.1, 0.4, 2.0], dtype=F64)
+    z = q2 * 1.5 ** 2
+    b1 = torch.sqrt(2 * z / (1 + z))
+    b2 = torch.sqrt(13 * z * z / (9 + 3 * z + z * z))
+    f1 = tdamp.blatt_weisskopf(1, q2, 1.5) * z.sqrt()
+    f2 = tdamp.blatt_weisskopf(2, q2, 1.5) * z
+    assert torch.allclose(f1 / b1, (f1 / b1)[0].expand(4), rtol=1e-14, atol=0)
+    assert torch.allclose(f2 / b2, (f2 / b2)[0].expand(4), rtol=1e-14, atol=0)
+
+
+def test_breakup_momentum_two_body_closed_form():
+    """q for K* -> K pi equals the momentum of either daughter in the rest frame,
+    from energy conservation E_K + E_pi = sqrt(s)."""
+    s = torch.tensor([0.8, 1.2], dtype=F64)
+    q = tdamp.breakup_q2(s, M_K ** 2, M_PI ** 2).sqrt()
+    e = torch.sqrt(q * q + M_K ** 2) + torch.sqrt(q * q + M_PI ** 2)
+    assert torch.allclose(e, s.sqrt(), rtol=1e-14, atol=0)
