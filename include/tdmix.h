@@ -1,0 +1,177 @@
+/*
+ * tdmix — time-dependent four-body amplitude likelihood on one GPU.
+ *
+ * C ABI of the library that evaluates the unbinned negative log-likelihood
+ * (NLL) of D0 -> K+ pi- pi+ pi- decay events and its gradient, as described
+ * in arXiv:1702.06735 (time-dependent amplitude analysis of a pseudoscalar
+ * decaying to four pseudoscalars):
+ *
+ *   rate     Eq. (mix), Sec. 2: for decay time t and phase-space point e,
+ *            dGamma/(e^{-Gamma t} N) = (|A|^2+|Abar|^2) cosh(y Gamma t)
+ *              + (|A|^2-|Abar|^2) cos(x Gamma t) - 2 Re(A Abar*) sinh(y Gamma t)
+ *              - 2 Im(A Abar*) sin(x Gamma t),
+ *            A (direct decay) and Abar (decay after D0 -> D0bar mixing)
+ *            being coherent sums sum_i c_i A_i over decay chains (Sec. 3),
+ *            each chain built from form (barrier) factors, a spin factor,
+ *            lineshapes and Bose symmetrisation of the two identical pi-.
+ *   norm     Sec. 3.1: normalisation N computed numerically, as the mean
+ *            over a flat phase-space Monte Carlo (MC) sample of the rate
+ *            integrated over t in [0, inf) in closed form.
+ *   NLL      -sum_{data} ln( e^{-Gamma t} B(e) / N ).
+ *
+ * Units: GeV, ps.  Final-state order: p0 = K+, p1 = pi-, p2 = pi+, p3 = pi-.
+ *
+ * Parameter vector (length tdmix_num_params):
+ *   [Re c_i, Im c_i] for every chain i in model order,
+ *   [m0_r, Gamma0_r] for every resonance r in model order,
+ *   x, y.
+ * Fixed parameters (see tdmix_set_floating) keep their place; their
+ * gradient entries are 0.
+ *
+ * Pointers: arguments documented as "host or device" may point to host
+ * memory (the call then synchronises with its stream and returns with the
+ * results written) or to device memory (the call is enqueued on the
+ * context's stream and returns immediately).  The kind is detected with
+ * cudaPointerGetAttributes.  Inputs are copied; outputs are written to the
+ * caller's buffers; the context owns all of its device memory.  No C++
+ * exception crosses this interface.  One context must not be used from two
+ * threads at the same time.
+ *
+ * Every function returning int returns a tdmix_status; on failure
+ * tdmix_last_error describes the cause.
+ */
+#ifndef TDMIX_H
+#define TDMIX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdmix_ctx tdmix_ctx;
+
+typedef enum {
+  TDMIX_OK = 0,
+  TDMIX_ERR_ARG = -1,       /* invalid argument or model description */
+  TDMIX_ERR_NOMEM = -2,     /* device or host allocation failed */
+  TDMIX_ERR_CUDA = -3,      /* a CUDA call failed */
+  TDMIX_ERR_STATE = -4,     /* no events loaded / wrong call order */
+  TDMIX_ERR_NONFINITE = -5, /* non-finite parameter, or a rate <= 0 / not finite */
+  TDMIX_ERR_DOMAIN = -6,    /* |y| >= 1, mass or width <= 0, pole below threshold */
+  TDMIX_ERR_TIMEOUT = -7,   /* a bounded wait gave up */
+  TDMIX_ERR_UNSUPPORTED = -8 /* model structure not compiled into this build */
+} tdmix_status;
+
+typedef enum {
+  TDMIX_FP64 = 0, /* every per-event quantity in float64 */
+  TDMIX_FP32 = 1  /* lineshapes, spin factors and coherent sums in float32;
+                     mixing terms, log-likelihood sum and normalisation
+                     accumulation in float64 */
+} tdmix_precision;
+
+/* One event sample in structure-of-arrays form.
+ *   n          number of events (>= 1)
+ *   p[a][c]    n doubles: component c (0:E, 1:px, 2:py, 3:pz) of final-state
+ *              particle a, GeV; 16 planes
+ *   t          n decay times in ps (data); NULL for phase-space MC
+ *   w          n MC event weights; NULL means weight 1 (ignored for data)
+ *   on_device  0: all pointers are host memory; 1: all are device memory */
+typedef struct {
+  int64_t n;
+  const double* p[4][4];
+  const double* t;
+  const double* w;
+  int on_device;
+} tdmix_events;
+
+/* Creates a context for an amplitude model (Sec. 3: resonances and decay
+ * chains assigned to A_f or Abar_f, JSON text; see the shipped model files
+ * for the schema) on the current CUDA device.  Recurring building blocks are
+ * shared (Sec. 3: recurring form factors, spin factors and lineshapes are
+ * linked to one instance).  *out receives the context; TDMIX_ERR_ARG for an
+ * invalid model, TDMIX_ERR_UNSUPPORTED if its structure was not compiled
+ * into this build. */
+int tdmix_create(const char* model_json, int precision, tdmix_ctx** out);
+
+/* Uses the given cudaStream_t (NULL: the legacy default stream) for all
+ * later work of the context. */
+int tdmix_set_stream(tdmix_ctx* ctx, void* cuda_stream);
+
+/* Length of the parameter vector, or a negative status. */
+int tdmix_num_params(const tdmix_ctx* ctx);
+
+/* Number of distinct per-event components a_j after sharing (the U of
+ * tdmix_norm_matrix), or a negative status. */
+int tdmix_num_components(const tdmix_ctx* ctx);
+
+/* Component index of chain `chain` (model order), or a negative status. */
+int tdmix_chain_component(const tdmix_ctx* ctx, int chain);
+
+/* Writes the model file's parameter values (host array, num_params). */
+int tdmix_default_params(const tdmix_ctx* ctx, double* out);
+
+/* Floating mask (host array of num_params ints, nonzero = floating).  The
+ * initial mask comes from the model file. */
+int tdmix_set_floating(tdmix_ctx* ctx, const int* mask);
+
+/* Loads the data sample (with decay times) and the phase-space MC sample
+ * used for the normalisation (Sec. 3.1), replacing earlier ones.  Copies the
+ * events and precomputes, once, every parameter-independent per-event
+ * quantity: invariant masses, width factors and spin x barrier factors.
+ * Either pointer may be NULL to keep the sample loaded before. */
+int tdmix_load_events(tdmix_ctx* ctx, const tdmix_events* data, const tdmix_events* mc);
+
+/* NLL at `params` (host or device, num_params doubles) into *nll_out (host
+ * or device) and, if grad_out is not NULL, its gradient (num_params doubles,
+ * host or device).  With host params, a call in which no mass or width moved
+ * since the previous call (and none floats, or no gradient is asked for)
+ * reuses the per-event component cache and the stored MC normalisation
+ * matrix; otherwise every step is recomputed.  Host outputs: returns
+ * TDMIX_ERR_NONFINITE / TDMIX_ERR_DOMAIN for invalid parameters or a rate
+ * <= 0.  Device outputs: such failures are reported as NaN values. */
+int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* grad_out);
+
+/* Per-event rate e^{-Gamma t} B(e) of Eq. (mix) for every data event
+ * (rates_out: host or device, n_data doubles) and, if norm_out is not NULL,
+ * the normalisation N (one double, same memory kind as rates_out). */
+int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, double* norm_out);
+
+/* Normalisation matrix I_jk = sum_e w_e a_j(e)^* a_k(e) / sum_e w_e of the
+ * components over the MC sample (Sec. 3.1), from the last evaluation that
+ * recomputed it; I_out (host) receives U*U complex numbers as interleaved
+ * (re, im) pairs, row-major in (j, k). */
+int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
+
+/* Kernel classes timed by tdmix_profile. */
+enum {
+  TDMIX_PROF_PREPARE = 0, /* per-evaluation constants from the parameters */
+  TDMIX_PROF_MC = 1,      /* MC pass: lineshapes, components, normalisation matrix, adjoint */
+  TDMIX_PROF_DATA = 2,    /* data pass: components (or cache), Eq. (mix), log sum, adjoint */
+  TDMIX_PROF_FINAL = 3,   /* fixed-order reduction, normalisation, NLL and gradient */
+  TDMIX_PROF_CLASSES = 4
+};
+
+/* Enables (1) or disables (0) timing of every kernel the context launches:
+ * a CUDA event pair is recorded on the context's stream around each launch.
+ * Library extension for measurement; not part of the paper's method. */
+int tdmix_profile(tdmix_ctx* ctx, int enable);
+
+/* Accumulated device time in ms (ms_out[TDMIX_PROF_CLASSES]) and launch
+ * counts (launches_out[TDMIX_PROF_CLASSES]) of the timed kernels since the
+ * last reset; synchronises with the recorded events.  reset != 0 clears the
+ * totals afterwards. */
+int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, int reset);
+
+/* Text of the last failure of this context (never NULL). */
+const char* tdmix_last_error(const tdmix_ctx* ctx);
+
+/* Releases the context and all of its device memory. */
+void tdmix_destroy(tdmix_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDMIX_H */

@@ -2,10 +2,12 @@
 
 TEST INFRASTRUCTURE (stored values): the chain structure is fixed below; the
 complex coefficients are drawn from the seeded Philox stream STREAM_COEF
-(|c| ~ U(0.5, 1.5), arg c ~ U(-pi, pi)), the first CF chain is the fixed
-reference 1 + 0i, and the DCS block (chains of A_f) is then rescaled with
-this oracle so that <|A_f|^2> / <|Abar_f|^2> = 0.0035 over a flat
-phase-space sample.  Run:  python -m oracle.make_models
+(r ~ U(0.5, 1.5), phi ~ U(-pi, pi)) and expressed relative to each chain's
+size: c_i = r_i e^{i phi_i} rms_0 / rms_i, with rms_i the root mean square
+of the chain amplitude over a flat phase-space sample, so that every chain
+contributes comparably (the convention behind fit fractions).  The first CF
+chain is the fixed reference 1 + 0i, and the DCS block (chains of A_f) is
+then rescaled so that <|A_f|^2> / <|Abar_f|^2> = 0.0035.  Run:  python -m oracle.make_models
 """
 from __future__ import annotations
 
@@ -76,7 +78,16 @@ def _draw_coefs(n, g):
 def _rescale_dcs(d, n_mc=200_000):
     m = tdamp.load_model(d)
     mc = samples.flat_phase_space(n_mc, samples.rng(99, samples.STREAM_MC))
-    A, Ab = tdamp.amplitudes(m, torch.from_numpy(mc), m.default_params())
+    with torch.no_grad():
+        rms = (tdamp.chain_amplitudes(m, torch.from_numpy(mc), m.default_params()).abs() ** 2).mean(0).sqrt()
+    ref = float(rms[0])
+    for i, c in enumerate(d["chains"]):
+        if i > 0:
+            k = ref / float(rms[i])
+            c["coef"] = [c["coef"][0] * k, c["coef"][1] * k]
+    m = tdamp.load_model(d)
+    with torch.no_grad():
+        A, Ab = tdamp.amplitudes(m, torch.from_numpy(mc), m.default_params())
     ratio = float((A.abs() ** 2).mean() / (Ab.abs() ** 2).mean())
     k = math.sqrt(DCS_TO_CF / ratio)
     for c in d["chains"]:

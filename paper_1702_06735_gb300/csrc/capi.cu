@@ -1,0 +1,612 @@
+// C ABI of the library: context, event loading, evaluation orchestration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/tdmix.h"
+#include "device_tables.hpp"
+#include "kernels.hpp"
+#include "model.hpp"
+
+namespace tdmix {
+const ShapeOps* find_shape_ops_f64(const std::string& sig);
+const ShapeOps* find_shape_ops_f32(const std::string& sig);
+const ShapeOps* find_shape_ops(const std::string& sig, bool f32) {
+  return f32 ? find_shape_ops_f32(sig) : find_shape_ops_f64(sig);
+}
+}  // namespace tdmix
+
+using namespace tdmix;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int64_t kPitchAlign = 256;
+
+struct Sample {
+  SampleDev dev{};
+  std::vector<void*> owned;
+  double* rates = nullptr;  // data: per-event rate scratch
+  bool loaded = false;
+};
+
+}  // namespace
+
+struct tdmix_ctx {
+  CompiledModel model;
+  bool f32 = false;
+  const ShapeOps* ops = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  DevModel* d_model = nullptr;
+  EvalConst* d_ec = nullptr;
+  double* d_params = nullptr;
+  double* d_result = nullptr;
+  double* d_gram = nullptr;
+  double* d_sumt = nullptr;
+  int* d_floating = nullptr;
+  double* h_params = nullptr;  // pinned
+  double* h_result = nullptr;  // pinned
+  double* d_rows_mc = nullptr;
+  double* d_rows_data = nullptr;
+  int rows_mc_cap = 0, rows_data_cap = 0;
+  Sample data, mc;
+  double sum_t = 0;
+  std::vector<int> floating;
+  std::vector<double> last_res;
+  bool cache_valid = false, gram_valid = false;
+  std::string err;
+  // kernel profiling: CUDA event pairs per kernel class, recorded on the stream
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev[TDMIX_PROF_CLASSES][2];
+  int prof_used[TDMIX_PROF_CLASSES] = {0, 0, 0, 0};
+  double prof_ms[TDMIX_PROF_CLASSES] = {0, 0, 0, 0};
+  int64_t prof_n[TDMIX_PROF_CLASSES] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int fail(tdmix_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define TDMIX_CK(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? TDMIX_ERR_NOMEM : TDMIX_ERR_CUDA,      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_sample(Sample& s) {
+  for (void* p : s.owned) cudaFree(p);
+  s.owned.clear();
+  s = Sample{};
+}
+
+int dalloc(tdmix_ctx* ctx, Sample& s, void** p, size_t bytes) {
+  TDMIX_CK(cudaMalloc(p, bytes < 16 ? 16 : bytes));
+  s.owned.push_back(*p);
+  return TDMIX_OK;
+}
+
+DevModel make_dev_model(const CompiledModel& m) {
+  DevModel d;
+  std::memset(&d, 0, sizeof d);
+  d.U = m.U;
+  d.NO = m.NO;
+  d.NB = m.NB();
+  d.NR = m.NR();
+  d.NS = m.NS();
+  d.NX = m.NX();
+  d.n_chains = int(m.chains.size());
+  d.n_params = m.n_params();
+  for (size_t c = 0; c < m.chains.size(); ++c) {
+    d.chain_comp[c] = m.chain_comp[c];
+    d.chain_amp[c] = m.chains[c].amp;
+  }
+  for (size_t r = 0; r < m.res.size(); ++r) {
+    d.res_shape[r] = m.res[r].shape;
+    d.res_L[r] = m.res[r].L;
+    d.res_ma[r] = m.res[r].ma;
+    d.res_mb[r] = m.res[r].mb;
+  }
+  d.r_res = m.r_res;
+  d.r_parent = m.r_parent;
+  d.gamma = 1.0 / m.tau;
+  for (size_t t = 0; t < m.terms.size(); ++t) {
+    d.term_spin[t] = m.terms[t].spin;
+    for (int k = 0; k < 4; ++k) d.term_parts[t][k] = m.terms[t].parts[k];
+  }
+  for (int s = 0; s < m.NS(); ++s) d.splane_mask[s] = m.splane_mask[s];
+  for (int x = 0; x < m.NX(); ++x) {
+    d.xplane_s[x] = m.xplanes[x].splane;
+    d.xplane_L[x] = m.xplanes[x].L;
+    d.xplane_ma[x] = m.xplanes[x].ma;
+    d.xplane_mb[x] = m.xplanes[x].mb;
+  }
+  return d;
+}
+
+// Host-side screening of a parameter vector (host pointer only).
+int check_params(tdmix_ctx* ctx, const double* p) {
+  const CompiledModel& m = ctx->model;
+  const int np = m.n_params(), nc = int(m.chains.size());
+  for (int k = 0; k < np; ++k)
+    if (!std::isfinite(p[k])) return fail(ctx, TDMIX_ERR_NONFINITE, "parameter " + std::to_string(k) + " is not finite");
+  for (int r = 0; r < m.NR(); ++r) {
+    if (m.res[r].shape == SHAPE_NONE) continue;
+    if (!(p[2 * nc + 2 * r] > 0) || !(p[2 * nc + 2 * r + 1] > 0))
+      return fail(ctx, TDMIX_ERR_DOMAIN, "resonance '" + m.res[r].name + "' needs a positive mass and width");
+  }
+  if (!(std::fabs(p[np - 1]) < 1.0)) return fail(ctx, TDMIX_ERR_DOMAIN, "|y| must be below 1");
+  return TDMIX_OK;
+}
+
+int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s) {
+  const CompiledModel& m = ctx->model;
+  if (ev->n < 1) return fail(ctx, TDMIX_ERR_ARG, "an event sample needs n >= 1");
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c)
+      if (!ev->p[a][c]) return fail(ctx, TDMIX_ERR_ARG, "missing momentum plane");
+  if (is_data && !ev->t) return fail(ctx, TDMIX_ERR_ARG, "the data sample needs decay times");
+  free_sample(s);
+  const int64_t n = ev->n;
+  const int64_t pitch = (n + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
+  const size_t es = ctx->f32 ? sizeof(float) : sizeof(double);
+  cudaStream_t st = ctx->stream;
+  int rc;
+  Momenta mom;
+  std::vector<void*> temps;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* p : temps) cudaFree(p);
+  };
+  if (ev->on_device) {
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) mom.p[a][c] = ev->p[a][c];
+  } else {
+    void* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, size_t(16) * n * sizeof(double));
+    if (e != cudaSuccess) return fail(ctx, TDMIX_ERR_NOMEM, "momentum staging buffer");
+    temps.push_back(buf);
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) {
+        double* dst = static_cast<double*>(buf) + size_t(a * 4 + c) * n;
+        e = cudaMemcpyAsync(dst, ev->p[a][c], n * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+          cleanup();
+          return fail(ctx, TDMIX_ERR_CUDA, std::string("momentum copy: ") + cudaGetErrorString(e));
+        }
+        mom.p[a][c] = dst;
+      }
+  }
+  SampleDev& d = s.dev;
+  d.n = n;
+  d.pitch = pitch;
+  const int NT = m.U * m.NO;
+  if ((rc = dalloc(ctx, s, &d.s, size_t(ctx->f32 ? 2 : 1) * m.NS() * pitch * es)) ||
+      (rc = dalloc(ctx, s, &d.x, size_t(m.NX()) * pitch * es)) ||
+      (rc = dalloc(ctx, s, &d.k, size_t(NT) * pitch * es))) {
+    cleanup();
+    free_sample(s);
+    return rc;
+  }
+  if (is_data) {
+    void* t = nullptr;
+    if ((rc = dalloc(ctx, s, &t, size_t(pitch) * sizeof(double))) ||
+        (rc = dalloc(ctx, s, &d.cache, size_t(2) * m.U * pitch * es)) ||
+        (rc = dalloc(ctx, s, reinterpret_cast<void**>(&s.rates), size_t(pitch) * sizeof(double)))) {
+      cleanup();
+      free_sample(s);
+      return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(t, ev->t, n * sizeof(double),
+                                    ev->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cleanup();
+      free_sample(s);
+      return fail(ctx, TDMIX_ERR_CUDA, std::string("time copy: ") + cudaGetErrorString(e));
+    }
+    d.t = static_cast<const double*>(t);
+  } else if (ev->w) {
+    void* w = nullptr;
+    if ((rc = dalloc(ctx, s, &w, size_t(pitch) * es))) {
+      cleanup();
+      free_sample(s);
+      return rc;
+    }
+    const double* wsrc = ev->w;
+    if (!ev->on_device) {
+      void* tmp = nullptr;
+      if (cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
+        cleanup();
+        free_sample(s);
+        return fail(ctx, TDMIX_ERR_NOMEM, "weight staging buffer");
+      }
+      temps.push_back(tmp);
+      cudaMemcpyAsync(tmp, ev->w, n * sizeof(double), cudaMemcpyHostToDevice, st);
+      wsrc = static_cast<const double*>(tmp);
+    }
+    if (ctx->f32) launch_to_f32(wsrc, static_cast<float*>(w), n, st);
+    else cudaMemcpyAsync(w, wsrc, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    d.w = w;
+  }
+  launch_precompute(ctx->f32, mom, n, pitch, ctx->d_model, d.s, d.x, d.k, st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && is_data) {
+    launch_sum(d.t, n, ctx->d_sumt, st);
+    e = cudaMemcpyAsync(&ctx->sum_t, ctx->d_sumt, sizeof(double), cudaMemcpyDeviceToHost, st);
+  }
+  cleanup();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    free_sample(s);
+    return fail(ctx, TDMIX_ERR_CUDA, std::string("precompute: ") + cudaGetErrorString(e));
+  }
+  s.loaded = true;
+  return TDMIX_OK;
+}
+
+constexpr int kProfPool = 4096;
+
+// Folds recorded event pairs into the accumulated times (synchronises).
+int prof_drain(tdmix_ctx* ctx) {
+  for (int c = 0; c < TDMIX_PROF_CLASSES; ++c) {
+    for (int k = 0; k < ctx->prof_used[c]; ++k) {
+      float ms = 0;
+      TDMIX_CK(cudaEventSynchronize(ctx->prof_ev[c][1][k]));
+      TDMIX_CK(cudaEventElapsedTime(&ms, ctx->prof_ev[c][0][k], ctx->prof_ev[c][1][k]));
+      ctx->prof_ms[c] += ms;
+      ctx->prof_n[c] += 1;
+    }
+    ctx->prof_used[c] = 0;
+  }
+  return TDMIX_OK;
+}
+
+// Records the start (phase 0) or end (phase 1) of a kernel of class c.
+int prof_mark(tdmix_ctx* ctx, int c, int phase) {
+  if (!ctx->prof_on) return TDMIX_OK;
+  if (phase == 0 && ctx->prof_used[c] == kProfPool) {
+    int rc = prof_drain(ctx);
+    if (rc) return rc;
+  }
+  const int k = ctx->prof_used[c];
+  TDMIX_CK(cudaEventRecord(ctx->prof_ev[c][phase][k], ctx->stream));
+  if (phase == 1) ctx->prof_used[c] = k + 1;
+  return TDMIX_OK;
+}
+
+int grid_for(tdmix_ctx* ctx, int64_t n, int bps) {
+  int64_t want = (n + kThreads - 1) / kThreads;
+  int64_t cap = int64_t(bps > 0 ? bps : 1) * ctx->num_sms;
+  return int(want < cap ? want : cap);
+}
+
+int ensure_rows(tdmix_ctx* ctx, double** buf, int* cap, int rows, int width) {
+  if (rows * width <= *cap) return TDMIX_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  TDMIX_CK(cudaMalloc(buf, size_t(rows) * width * sizeof(double)));
+  *cap = rows * width;
+  return TDMIX_OK;
+}
+
+// One evaluation: enqueue everything, leave the result in ctx->d_result.
+int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool want_grad, double* rates) {
+  const CompiledModel& m = ctx->model;
+  const int np = m.n_params(), nc = int(m.chains.size());
+  cudaStream_t st = ctx->stream;
+  if (!ctx->data.loaded || !ctx->mc.loaded) return fail(ctx, TDMIX_ERR_STATE, "load data and MC events first");
+  bool res_floating = false;
+  for (int k = 2 * nc; k < 2 * nc + 2 * m.NR(); ++k) res_floating |= ctx->floating[k] != 0;
+  bool full = !host_params || !ctx->cache_valid || (want_grad && res_floating);
+  if (host_params && !full) {
+    for (int k = 0; k < 2 * m.NR(); ++k)
+      if (params[2 * nc + k] != ctx->last_res[k]) full = true;
+  }
+  if (host_params) {
+    std::memcpy(ctx->h_params, params, np * sizeof(double));
+    TDMIX_CK(cudaMemcpyAsync(ctx->d_params, ctx->h_params, np * sizeof(double), cudaMemcpyHostToDevice, st));
+  } else {
+    TDMIX_CK(cudaMemcpyAsync(ctx->d_params, params, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  int rc;
+  if ((rc = prof_mark(ctx, TDMIX_PROF_PREPARE, 0))) return rc;
+  launch_prepare(ctx->d_params, ctx->d_model, ctx->d_ec, st);
+  TDMIX_CK(cudaGetLastError());
+  if ((rc = prof_mark(ctx, TDMIX_PROF_PREPARE, 1))) return rc;
+  const ShapeOps* ops = ctx->ops;
+  FinalArgs fa{};
+  fa.dm = ctx->d_model;
+  fa.ec = ctx->d_ec;
+  fa.gram_store = ctx->d_gram;
+  fa.n_data = ctx->data.dev.n;
+  fa.sum_t = ctx->sum_t;
+  fa.floating = ctx->d_floating;
+  fa.want_grad = want_grad;
+  fa.have_res_grad = full && want_grad;
+  fa.result = ctx->d_result;
+  if (full) {
+    const int gmc = grid_for(ctx, ctx->mc.dev.n, ops->mc_blocks_per_sm(want_grad));
+    if ((rc = ensure_rows(ctx, &ctx->d_rows_mc, &ctx->rows_mc_cap, gmc, ops->mc_row_width))) return rc;
+    if ((rc = prof_mark(ctx, TDMIX_PROF_MC, 0))) return rc;
+    TDMIX_CK(ops->mc(want_grad, gmc, st, ctx->mc.dev, ctx->d_ec, ctx->d_rows_mc));
+    if ((rc = prof_mark(ctx, TDMIX_PROF_MC, 1))) return rc;
+    fa.mc_rows = ctx->d_rows_mc;
+    fa.n_mc_rows = gmc;
+  } else {
+    fa.mc_rows = nullptr;
+    fa.n_mc_rows = 0;
+  }
+  const int gd = grid_for(ctx, ctx->data.dev.n, ops->data_blocks_per_sm(!full, want_grad));
+  if ((rc = ensure_rows(ctx, &ctx->d_rows_data, &ctx->rows_data_cap, gd, ops->data_row_width))) return rc;
+  if ((rc = prof_mark(ctx, TDMIX_PROF_DATA, 0))) return rc;
+  TDMIX_CK(ops->data(!full, want_grad, gd, st, ctx->data.dev, ctx->d_ec, ctx->d_rows_data, rates));
+  if ((rc = prof_mark(ctx, TDMIX_PROF_DATA, 1))) return rc;
+  fa.data_rows = ctx->d_rows_data;
+  fa.n_data_rows = gd;
+  if ((rc = prof_mark(ctx, TDMIX_PROF_FINAL, 0))) return rc;
+  launch_final(fa, st);
+  TDMIX_CK(cudaGetLastError());
+  if ((rc = prof_mark(ctx, TDMIX_PROF_FINAL, 1))) return rc;
+  if (full) {
+    ctx->gram_valid = true;
+    ctx->cache_valid = true;
+    if (host_params) ctx->last_res.assign(params + 2 * nc, params + 2 * nc + 2 * m.NR());
+    else ctx->cache_valid = false;  // parameter values unknown on the host
+  }
+  return TDMIX_OK;
+}
+
+int result_status(tdmix_ctx* ctx) {
+  const double* r = ctx->h_result;
+  if (r[2] < 0) {
+    int st = int(r[2]);
+    return fail(ctx, st, st == TDMIX_ERR_DOMAIN ? "parameter outside its domain (|y| < 1, m0 > 0, Gamma0 > 0, "
+                                                  "pole above the decay threshold)"
+                                                : "non-finite parameter");
+  }
+  if (r[2] > 0)
+    return fail(ctx, TDMIX_ERR_NONFINITE, std::to_string(int64_t(r[2])) + " data events have a rate <= 0 or not finite");
+  if (!(r[1] > 0) || !std::isfinite(r[0])) return fail(ctx, TDMIX_ERR_NONFINITE, "normalisation <= 0 or NLL not finite");
+  return TDMIX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
+  if (!out || !model_json) return TDMIX_ERR_ARG;
+  *out = nullptr;
+  if (precision != TDMIX_FP64 && precision != TDMIX_FP32) return TDMIX_ERR_ARG;
+  tdmix_ctx* ctx = new (std::nothrow) tdmix_ctx;
+  if (!ctx) return TDMIX_ERR_NOMEM;
+  try {
+    ctx->model = compile_model(model_json);
+  } catch (const std::exception& e) {
+    // keep a context alive only to carry the message
+    ctx->err = e.what();
+    *out = ctx;
+    return TDMIX_ERR_ARG;
+  }
+  ctx->f32 = precision == TDMIX_FP32;
+  ctx->ops = find_shape_ops(ctx->model.signature(), ctx->f32);
+  *out = ctx;
+  if (!ctx->ops)
+    return fail(ctx, TDMIX_ERR_UNSUPPORTED,
+                "model structure not compiled into this build (add the model file and rebuild): " +
+                    ctx->model.signature());
+  TDMIX_CK(cudaGetDevice(&ctx->device));
+  TDMIX_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int np = ctx->model.n_params();
+  TDMIX_CK(cudaMalloc(&ctx->d_model, sizeof(DevModel)));
+  TDMIX_CK(cudaMalloc(&ctx->d_ec, sizeof(EvalConst)));
+  TDMIX_CK(cudaMalloc(&ctx->d_params, np * sizeof(double)));
+  TDMIX_CK(cudaMalloc(&ctx->d_result, (kResHeader + np) * sizeof(double)));
+  TDMIX_CK(cudaMalloc(&ctx->d_gram, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes) * sizeof(double)));
+  TDMIX_CK(cudaMalloc(&ctx->d_sumt, sizeof(double)));
+  TDMIX_CK(cudaMalloc(&ctx->d_floating, np * sizeof(int)));
+  TDMIX_CK(cudaMallocHost(&ctx->h_params, np * sizeof(double)));
+  TDMIX_CK(cudaMallocHost(&ctx->h_result, (kResHeader + np) * sizeof(double)));
+  DevModel dm = make_dev_model(ctx->model);
+  TDMIX_CK(cudaMemcpy(ctx->d_model, &dm, sizeof dm, cudaMemcpyHostToDevice));
+  ctx->floating = ctx->model.floating_mask();
+  TDMIX_CK(cudaMemcpy(ctx->d_floating, ctx->floating.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  return TDMIX_OK;
+}
+
+int tdmix_set_stream(tdmix_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return TDMIX_ERR_ARG;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return TDMIX_OK;
+}
+
+int tdmix_num_params(const tdmix_ctx* ctx) { return ctx ? ctx->model.n_params() : TDMIX_ERR_ARG; }
+
+int tdmix_num_components(const tdmix_ctx* ctx) { return ctx ? ctx->model.U : TDMIX_ERR_ARG; }
+
+int tdmix_chain_component(const tdmix_ctx* ctx, int chain) {
+  if (!ctx || chain < 0 || chain >= int(ctx->model.chains.size())) return TDMIX_ERR_ARG;
+  return ctx->model.chain_comp[chain];
+}
+
+int tdmix_default_params(const tdmix_ctx* ctx, double* out) {
+  if (!ctx || !out) return TDMIX_ERR_ARG;
+  std::vector<double> p = ctx->model.default_params();
+  std::memcpy(out, p.data(), p.size() * sizeof(double));
+  return TDMIX_OK;
+}
+
+int tdmix_set_floating(tdmix_ctx* ctx, const int* mask) {
+  if (!ctx || !mask) return TDMIX_ERR_ARG;
+  if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  const int np = ctx->model.n_params();
+  for (int k = 0; k < np; ++k) ctx->floating[k] = mask[k] != 0;
+  TDMIX_CK(cudaMemcpy(ctx->d_floating, ctx->floating.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  return TDMIX_OK;
+}
+
+int tdmix_load_events(tdmix_ctx* ctx, const tdmix_events* data, const tdmix_events* mc) {
+  if (!ctx) return TDMIX_ERR_ARG;
+  if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  int rc;
+  if (data && (rc = load_sample(ctx, data, true, ctx->data))) return rc;
+  if (mc && (rc = load_sample(ctx, mc, false, ctx->mc))) return rc;
+  ctx->cache_valid = false;
+  if (mc) ctx->gram_valid = false;
+  return TDMIX_OK;
+}
+
+int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* grad_out) {
+  if (!ctx || !params || !nll_out) return fail(ctx, TDMIX_ERR_ARG, "null argument");
+  if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  const bool host_params = !is_device_ptr(params);
+  const bool host_out = !is_device_ptr(nll_out);
+  if (grad_out && is_device_ptr(grad_out) == host_out)
+    return fail(ctx, TDMIX_ERR_ARG, "nll_out and grad_out must both be host or both be device memory");
+  int rc;
+  if (host_params && (rc = check_params(ctx, params))) return rc;
+  if ((rc = enqueue_eval(ctx, params, host_params, grad_out != nullptr, nullptr))) return rc;
+  const int np = ctx->model.n_params();
+  cudaStream_t st = ctx->stream;
+  if (host_out) {
+    TDMIX_CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, (kResHeader + np) * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    TDMIX_CK(cudaStreamSynchronize(st));
+    *nll_out = ctx->h_result[0];
+    if (grad_out) std::memcpy(grad_out, ctx->h_result + kResHeader, np * sizeof(double));
+    return result_status(ctx);
+  }
+  TDMIX_CK(cudaMemcpyAsync(nll_out, ctx->d_result, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (grad_out)
+    TDMIX_CK(cudaMemcpyAsync(grad_out, ctx->d_result + kResHeader, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return TDMIX_OK;
+}
+
+int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, double* norm_out) {
+  if (!ctx || !params || !rates_out) return fail(ctx, TDMIX_ERR_ARG, "null argument");
+  if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  const bool host_params = !is_device_ptr(params);
+  const bool host_out = !is_device_ptr(rates_out);
+  int rc;
+  if (host_params && (rc = check_params(ctx, params))) return rc;
+  if (!ctx->data.loaded) return fail(ctx, TDMIX_ERR_STATE, "load data and MC events first");
+  double* rates = host_out ? ctx->data.rates : rates_out;
+  if ((rc = enqueue_eval(ctx, params, host_params, false, rates))) return rc;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = ctx->data.dev.n;
+  if (host_out) {
+    TDMIX_CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, kResHeader * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TDMIX_CK(cudaMemcpyAsync(rates_out, rates, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TDMIX_CK(cudaStreamSynchronize(st));
+    if (norm_out) *norm_out = ctx->h_result[1];
+    if (ctx->h_result[2] < 0) return result_status(ctx);
+    return TDMIX_OK;
+  }
+  if (norm_out) TDMIX_CK(cudaMemcpyAsync(norm_out, ctx->d_result + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return TDMIX_OK;
+}
+
+int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out) {
+  if (!ctx || !I_out) return fail(ctx, TDMIX_ERR_ARG, "null argument");
+  if (!ctx->gram_valid) return fail(ctx, TDMIX_ERR_STATE, "no evaluation has computed the normalisation matrix yet");
+  const int U = ctx->model.U;
+  const int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2;
+  std::vector<double> row(1 + NRE + NIM);
+  TDMIX_CK(cudaMemcpyAsync(row.data(), ctx->d_gram, row.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TDMIX_CK(cudaStreamSynchronize(ctx->stream));
+  const double sw = row[0];
+  int ir = 0, ii = 0;
+  for (int j = 0; j < U; ++j)
+    for (int k = j; k < U; ++k) {
+      const double re = row[1 + ir++] / sw;
+      const double im = k > j ? row[1 + NRE + ii++] / sw : 0.0;
+      I_out[2 * (j * U + k)] = re;
+      I_out[2 * (j * U + k) + 1] = im;
+      I_out[2 * (k * U + j)] = re;
+      I_out[2 * (k * U + j) + 1] = -im;
+    }
+  return TDMIX_OK;
+}
+
+int tdmix_profile(tdmix_ctx* ctx, int enable) {
+  if (!ctx) return TDMIX_ERR_ARG;
+  if (enable && ctx->prof_ev[0][0].empty()) {
+    for (int c = 0; c < TDMIX_PROF_CLASSES; ++c)
+      for (int ph = 0; ph < 2; ++ph) {
+        ctx->prof_ev[c][ph].resize(kProfPool);
+        for (auto& e : ctx->prof_ev[c][ph]) TDMIX_CK(cudaEventCreate(&e));
+      }
+  }
+  if (!enable) {
+    int rc = prof_drain(ctx);
+    if (rc) return rc;
+  }
+  ctx->prof_on = enable != 0;
+  return TDMIX_OK;
+}
+
+int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, int reset) {
+  if (!ctx || !ms_out || !launches_out) return fail(ctx, TDMIX_ERR_ARG, "null argument");
+  int rc = prof_drain(ctx);
+  if (rc) return rc;
+  for (int c = 0; c < TDMIX_PROF_CLASSES; ++c) {
+    ms_out[c] = ctx->prof_ms[c];
+    launches_out[c] = ctx->prof_n[c];
+    if (reset) {
+      ctx->prof_ms[c] = 0;
+      ctx->prof_n[c] = 0;
+    }
+  }
+  return TDMIX_OK;
+}
+
+const char* tdmix_last_error(const tdmix_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void tdmix_destroy(tdmix_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->ops) cudaStreamSynchronize(ctx->stream);
+  free_sample(ctx->data);
+  free_sample(ctx->mc);
+  cudaFree(ctx->d_model);
+  cudaFree(ctx->d_ec);
+  cudaFree(ctx->d_params);
+  cudaFree(ctx->d_result);
+  cudaFree(ctx->d_gram);
+  cudaFree(ctx->d_sumt);
+  cudaFree(ctx->d_floating);
+  cudaFree(ctx->d_rows_mc);
+  cudaFree(ctx->d_rows_data);
+  if (ctx->h_params) cudaFreeHost(ctx->h_params);
+  if (ctx->h_result) cudaFreeHost(ctx->h_result);
+  for (int c = 0; c < TDMIX_PROF_CLASSES; ++c)
+    for (int ph = 0; ph < 2; ++ph)
+      for (auto& e : ctx->prof_ev[c][ph]) cudaEventDestroy(e);
+  delete ctx;
+}
+
+}  // extern "C"

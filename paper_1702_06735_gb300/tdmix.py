@@ -1,0 +1,248 @@
+"""Python binding of the tdmix C ABI (include/tdmix.h) via ctypes.
+
+Argument marshalling only: every step of the likelihood runs in the CUDA
+kernels of libtdmix.so.  Importing this module does not load the library;
+the first use does, and raises if it was not built (there is no CPU
+fallback).  Host (NumPy) and device (torch CUDA) arrays are accepted.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdmix.so")
+MODEL_DIR = os.path.join(HERE, "amplitude_models")
+
+FP64, FP32 = 0, 1
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_STATE", -5: "ERR_NONFINITE",
+          -6: "ERR_DOMAIN", -7: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
+
+# Every function the header declares, with its ctypes signature.
+_c_p = ctypes.c_void_p
+_c_i = ctypes.c_int
+_SIGNATURES = {
+    "tdmix_create": (_c_i, [ctypes.c_char_p, _c_i, ctypes.POINTER(_c_p)]),
+    "tdmix_set_stream": (_c_i, [_c_p, _c_p]),
+    "tdmix_num_params": (_c_i, [_c_p]),
+    "tdmix_num_components": (_c_i, [_c_p]),
+    "tdmix_chain_component": (_c_i, [_c_p, _c_i]),
+    "tdmix_default_params": (_c_i, [_c_p, _c_p]),
+    "tdmix_set_floating": (_c_i, [_c_p, _c_p]),
+    "tdmix_load_events": (_c_i, [_c_p, _c_p, _c_p]),
+    "tdmix_nll": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
+    "tdmix_event_rates": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
+    "tdmix_norm_matrix": (_c_i, [_c_p, _c_p]),
+    "tdmix_profile": (_c_i, [_c_p, _c_i]),
+    "tdmix_profile_read": (_c_i, [_c_p, _c_p, _c_p, _c_i]),
+    "tdmix_last_error": (ctypes.c_char_p, [_c_p]),
+    "tdmix_destroy": (None, [_c_p]),
+}
+
+_lib = None
+
+
+class TDMixError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libtdmix.so (built by ``paper_1702_06735_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1702_06735_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class Events(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("p", ctypes.c_void_p * 16), ("t", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+def model_json(model) -> str:
+    """JSON text of a model given as a shipped name, a path, a dict or text."""
+    if isinstance(model, dict):
+        return json.dumps(model)
+    if isinstance(model, str):
+        if model.lstrip().startswith("{"):
+            return model
+        path = model if os.path.exists(model) else os.path.join(MODEL_DIR, model + ".json")
+        with open(path) as f:
+            return f.read()
+    raise TypeError("model must be a name, path, dict or JSON text")
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _planes(p4, t=None, w=None):
+    """Marshals (n, 4, 4) momenta (+ times, weights) into an Events struct.
+    Returns (struct, keep-alive list)."""
+    ev = Events()
+    keep = []
+    if _is_torch(p4) and p4.is_cuda:
+        import torch
+        planes = p4.to(torch.float64).permute(1, 2, 0).contiguous()
+        n = planes.shape[-1]
+        keep.append(planes)
+        base = planes.data_ptr()
+        for k in range(16):
+            ev.p[k] = base + k * n * 8
+        for name, arr in (("t", t), ("w", w)):
+            if arr is not None:
+                a = arr.to(device=planes.device, dtype=torch.float64).contiguous()
+                keep.append(a)
+                setattr(ev, name, a.data_ptr())
+        ev.on_device = 1
+    else:
+        planes = np.ascontiguousarray(np.transpose(np.asarray(p4, dtype=np.float64), (1, 2, 0)))
+        n = planes.shape[-1]
+        keep.append(planes)
+        base = planes.ctypes.data
+        for k in range(16):
+            ev.p[k] = base + k * n * 8
+        for name, arr in (("t", t), ("w", w)):
+            if arr is not None:
+                a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64))
+                keep.append(a)
+                setattr(ev, name, a.ctypes.data)
+        ev.on_device = 0
+    ev.n = n
+    return ev, keep
+
+
+class TDMix:
+    """One likelihood context (tdmix_ctx) on the current CUDA device."""
+
+    def __init__(self, model, precision: str = "fp64", stream=None):
+        self._lib = load_library()
+        self._ctx = ctypes.c_void_p()
+        prec = {"fp64": FP64, "fp32": FP32}[precision]
+        self.precision = precision
+        rc = self._lib.tdmix_create(model_json(model).encode(), prec, ctypes.byref(self._ctx))
+        if rc != 0:
+            msg = self._lib.tdmix_last_error(self._ctx).decode() if self._ctx else ""
+            if self._ctx:
+                self._lib.tdmix_destroy(self._ctx)
+                self._ctx = ctypes.c_void_p()
+            raise TDMixError(rc, msg)
+        if stream is not None:
+            self.set_stream(stream)
+        self.n_params = self._lib.tdmix_num_params(self._ctx)
+        self.n_components = self._lib.tdmix_num_components(self._ctx)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TDMixError(rc, self._lib.tdmix_last_error(self._ctx).decode())
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self._lib.tdmix_set_stream(self._ctx, handle))
+
+    def chain_component(self, chain: int) -> int:
+        c = self._lib.tdmix_chain_component(self._ctx, chain)
+        if c < 0:
+            self._check(c)
+        return c
+
+    def default_params(self) -> np.ndarray:
+        out = np.empty(self.n_params)
+        self._check(self._lib.tdmix_default_params(self._ctx, out.ctypes.data))
+        return out
+
+    def set_floating(self, mask):
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.int32))
+        if m.shape != (self.n_params,):
+            raise ValueError("mask length must equal the number of parameters")
+        self._check(self._lib.tdmix_set_floating(self._ctx, m.ctypes.data))
+
+    def load_events(self, data_p4=None, data_t=None, mc_p4=None, mc_w=None):
+        keep = []
+        d = m = None
+        if data_p4 is not None:
+            d, k = _planes(data_p4, t=data_t)
+            keep += k
+        if mc_p4 is not None:
+            m, k = _planes(mc_p4, w=mc_w)
+            keep += k
+        self._check(self._lib.tdmix_load_events(self._ctx, ctypes.byref(d) if d else None,
+                                                ctypes.byref(m) if m else None))
+        if data_p4 is not None:
+            self._nd = int(data_p4.shape[0])
+
+    def nll(self, params, grad: bool = True):
+        """NLL (and gradient) at host parameters; returns (float, ndarray|None)."""
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        if p.shape != (self.n_params,):
+            raise ValueError("parameter vector has the wrong length")
+        out = np.empty(1)
+        g = np.empty(self.n_params) if grad else None
+        self._check(self._lib.tdmix_nll(self._ctx, p.ctypes.data, out.ctypes.data,
+                                        g.ctypes.data if grad else None))
+        return float(out[0]), g
+
+    def nll_device(self, params, nll_out, grad_out=None):
+        """Enqueues an evaluation with device tensors (float64) on the context's stream."""
+        self._check(self._lib.tdmix_nll(self._ctx, params.data_ptr(), nll_out.data_ptr(),
+                                        grad_out.data_ptr() if grad_out is not None else None))
+
+    def event_rates(self, params):
+        """(per-event rate e^{-Gamma t} B of every data event, normalisation N)."""
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        n = self._n_data
+        rates = np.empty(n)
+        norm = np.empty(1)
+        self._check(self._lib.tdmix_event_rates(self._ctx, p.ctypes.data, rates.ctypes.data, norm.ctypes.data))
+        return rates, float(norm[0])
+
+    @property
+    def _n_data(self):
+        if not hasattr(self, "_nd"):
+            raise RuntimeError("load events first")
+        return self._nd
+
+    def norm_matrix(self) -> np.ndarray:
+        U = self.n_components
+        out = np.empty(2 * U * U)
+        self._check(self._lib.tdmix_norm_matrix(self._ctx, out.ctypes.data))
+        return (out[0::2] + 1j * out[1::2]).reshape(U, U)
+
+    PROF_CLASSES = ("prepare", "mc", "data", "final")
+
+    def profile(self, enable: bool = True):
+        """Times every kernel launch of this context with CUDA events."""
+        self._check(self._lib.tdmix_profile(self._ctx, int(enable)))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{kernel class: (total ms, launches)} since the last reset."""
+        ms = np.zeros(4)
+        n = np.zeros(4, dtype=np.int64)
+        self._check(self._lib.tdmix_profile_read(self._ctx, ms.ctypes.data, n.ctypes.data, int(reset)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROF_CLASSES)}
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.tdmix_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,160 @@
+"""CUDA path (through the C ABI) against the oracle on the same seeded inputs.
+
+Tolerances: fp64 path 1e-12 relative (per-event rates relative to their
+cancellation-free scale, see workloads.rate_scale); fp32 precision path
+1e-5 relative per-event rate and 1e-3 absolute NLL at 50,000 events."""
+import numpy as np
+import pytest
+import torch
+
+from conftest import model_path
+from oracle import tdamp
+from workloads import perturbed_params, rate_scale, workload
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("d0_k3pi_2chain", 1000, 10_000, 0), ("d0_k3pi_full", 777, 6_001, 1)]
+
+
+def _ctx(name, precision, data, t, mc, w=None):
+    from paper_1702_06735_gb300.tdmix import TDMix
+    c = TDMix(name, precision)
+    c.load_events(data, t, mc, w)
+    return c
+
+
+def _oracle(m, data, t, mc, p, w=None):
+    v, g = tdamp.nll_and_grad(m, torch.from_numpy(data), torch.from_numpy(t), torch.from_numpy(mc), p,
+                              None if w is None else torch.from_numpy(w))
+    with torch.no_grad():
+        R = tdamp.event_rates(m, torch.from_numpy(data), torch.from_numpy(t), torch.as_tensor(p)).numpy()
+        N = float(tdamp.normalisation(m, torch.from_numpy(mc), torch.as_tensor(p),
+                                      None if w is None else torch.from_numpy(w)))
+    return v, g.numpy(), R, N
+
+
+@pytest.mark.parametrize("name,nd,nm,wid", CASES)
+@pytest.mark.parametrize("moved", [False, True])
+def test_fp64_parity(name, nd, nm, wid, moved):
+    m, data, t, mc = workload(name, nd, nm, wid)
+    p = perturbed_params(m, 7 + wid) if moved else m.default_params().numpy()
+    v0, g0, R0, N0 = _oracle(m, data, t, mc, p)
+    c = _ctx(name, "fp64", data, t, mc)
+    R, N = c.event_rates(p)
+    sc = rate_scale(m, data, t, p)
+    assert np.max(np.abs(R - R0) / sc) <= 1e-12
+    assert abs(N / N0 - 1) <= 1e-12
+    v, g = c.nll(p)
+    assert abs(v - v0) <= 1e-12 * abs(v0)
+    gs = np.maximum(np.abs(g0), 1e-3 * np.max(np.abs(g0)))
+    assert np.max(np.abs(g - g0) / gs) <= 1e-9, np.abs(g - g0) / gs
+
+
+@pytest.mark.parametrize("name,nd,nm,wid", CASES)
+def test_norm_matrix_parity(name, nd, nm, wid):
+    m, data, t, mc = workload(name, nd, nm, wid)
+    p = perturbed_params(m, 11)
+    c = _ctx(name, "fp64", data, t, mc)
+    c.nll(p)
+    I = c.norm_matrix()
+    Ich = tdamp.component_gram(m, torch.from_numpy(mc), torch.as_tensor(p)).numpy()
+    comp = [c.chain_component(i) for i in range(len(m.chains))]
+    ref = np.zeros_like(I)
+    for i, ci in enumerate(comp):
+        for k, ck in enumerate(comp):
+            ref[ci, ck] = Ich[i, k]
+    assert np.max(np.abs(I - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("name,nd,nm,wid", CASES)
+def test_cached_path_matches_full_path(name, nd, nm, wid):
+    """Moving only coefficients and x, y reuses the component cache and the
+    stored normalisation matrix; results still equal the oracle."""
+    m, data, t, mc = workload(name, nd, nm, wid)
+    c = _ctx(name, "fp64", data, t, mc)
+    mask = m.floating_mask().numpy().astype(np.int32)
+    nc = len(m.chains)
+    mask[2 * nc:2 * nc + 2 * len(m.resonances)] = 0   # fixed model: the cache applies
+    c.set_floating(mask)
+    p0 = m.default_params().numpy()
+    c.nll(p0)
+    p1 = perturbed_params(m, 12, masses=False)
+    v, g = c.nll(p1)
+    v0, g0, _, _ = _oracle(m, data, t, mc, p1)
+    g0 = np.where(mask.astype(bool), g0, 0.0)
+    assert abs(v - v0) <= 1e-12 * abs(v0)
+    gs = np.maximum(np.abs(g0), 1e-3 * np.max(np.abs(g0)))
+    assert np.max(np.abs(g - g0) / gs) <= 1e-9
+
+
+def test_weighted_mc_and_ragged_tiny_samples():
+    m, data, t, mc = workload("d0_k3pi_2chain", 1000, 10_000, 0)
+    w = np.random.default_rng(4).uniform(0.5, 2.0, 257)
+    for nd, nm in ((1, 1), (3, 257), (255, 513)):
+        ww = w[:nm] if nm == 257 else None
+        c = _ctx("d0_k3pi_2chain", "fp64", data[:nd], t[:nd], mc[:nm], ww)
+        p = perturbed_params(m, 13)
+        v, g = c.nll(p)
+        v0, g0, _, _ = _oracle(m, data[:nd], t[:nd], mc[:nm], p, ww)
+        assert abs(v - v0) <= 1e-12 * max(1.0, abs(v0))
+
+
+def test_repeatable_bitwise():
+    m, data, t, mc = workload("d0_k3pi_full", 777, 6_001, 1)
+    c = _ctx("d0_k3pi_full", "fp64", data, t, mc)
+    p = perturbed_params(m, 14)
+    a = c.nll(p)
+    b = c.nll(p)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_invalid_parameters_are_reported():
+    from paper_1702_06735_gb300.tdmix import TDMixError
+    m, data, t, mc = workload("d0_k3pi_2chain", 1000, 10_000, 0)
+    c = _ctx("d0_k3pi_2chain", "fp64", data, t, mc)
+    p = m.default_params().numpy()
+    bad = p.copy()
+    bad[2] = np.nan
+    with pytest.raises(TDMixError) as e:
+        c.nll(bad)
+    assert e.value.code == -5
+    bad = p.copy()
+    bad[-1] = 1.5
+    with pytest.raises(TDMixError) as e:
+        c.nll(bad)
+    assert e.value.code == -6
+    bad = p.copy()
+    bad[5] = -0.1   # negative width
+    with pytest.raises(TDMixError) as e:
+        c.nll(bad)
+    assert e.value.code == -6
+    v, _ = c.nll(p)       # still usable
+    assert np.isfinite(v)
+
+
+def test_device_pointer_path_matches_host_path():
+    m, data, t, mc = workload("d0_k3pi_full", 777, 6_001, 1)
+    dev = torch.device("cuda:0")
+    c = _ctx("d0_k3pi_full", "fp64", torch.from_numpy(data).to(dev), torch.from_numpy(t).to(dev),
+             torch.from_numpy(mc).to(dev))
+    p = perturbed_params(m, 15)
+    vh, gh = c.nll(p)
+    pd = torch.from_numpy(p).to(dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    gd = torch.empty(len(p), dtype=torch.float64, device=dev)
+    c.nll_device(pd, out, gd)
+    torch.cuda.synchronize()
+    assert float(out[0]) == vh and np.array_equal(gd.cpu().numpy(), gh)
+
+
+@pytest.mark.parametrize("name,nd,nm,wid", CASES)
+def test_fp32_precision_path(name, nd, nm, wid):
+    m, data, t, mc = workload(name, nd, nm, wid)
+    p = perturbed_params(m, 16)
+    v0, g0, R0, N0 = _oracle(m, data, t, mc, p)
+    c = _ctx(name, "fp32", data, t, mc)
+    R, N = c.event_rates(p)
+    rel = np.abs(R / R0 - 1)
+    assert np.max(rel) <= 1e-5, (np.max(rel), np.median(rel))
+    v, g = c.nll(p)
+    assert abs(v - v0) <= 1e-3, (v, v0)

@@ -1,0 +1,61 @@
+"""Seeded test workloads: flat phase-space MC and time-dependent pseudo-data
+generated by accept/reject with the ORACLE's rate (never the CUDA path)."""
+import functools
+
+import numpy as np
+import torch
+
+from conftest import model_path
+from oracle import tdamp
+from paper_1702_06735_gb300 import samples
+
+
+def oracle_rate_fn(model, params=None):
+    p = model.default_params() if params is None else torch.as_tensor(params, dtype=torch.float64)
+
+    def f(p4, t):
+        with torch.no_grad():
+            return tdamp.event_rates(model, torch.from_numpy(p4), torch.from_numpy(t), p).numpy()
+    return f
+
+
+@functools.lru_cache(maxsize=None)
+def workload(name: str, n_data: int, n_mc: int, workload_id: int):
+    """(model, data_p4, data_t, mc_p4) for a shipped model."""
+    m = tdamp.load_model(model_path(name))
+    gd = samples.rng(workload_id, samples.STREAM_DATA)
+    gm = samples.rng(workload_id, samples.STREAM_MC)
+    data, t, _ = samples.generate_time_dependent(n_data, gd, oracle_rate_fn(m), m.gamma, m.y,
+                                                 pilot=min(50_000, 20 * n_data), batch=1 << 15)
+    mc = samples.flat_phase_space(n_mc, gm)
+    return m, data, t, mc
+
+
+def perturbed_params(model, seed: int, scale: float = 0.05, masses: bool = True):
+    """Parameters moved away from the model file's values (seeded)."""
+    g = np.random.default_rng(seed)
+    p = model.default_params().numpy().copy()
+    nc, nr = len(model.chains), len(model.resonances)
+    mask = model.floating_mask().numpy()
+    for k in range(2 * nc):
+        if mask[k]:
+            p[k] *= 1 + scale * g.normal()
+    if masses:
+        for r in range(nr):
+            p[2 * nc + 2 * r] *= 1 + 0.1 * scale * g.normal()
+            p[2 * nc + 2 * r + 1] *= 1 + scale * g.normal()
+    p[-2] += 0.002 * g.normal()
+    p[-1] += 0.002 * g.normal()
+    return p
+
+
+def rate_scale(model, data, t, params):
+    """Rounding scale of each event's rate: 2 e^{-G t} cosh(y G t) (sum |c_i A_i|)^2,
+    an upper bound of |rate| obtained without cancellation."""
+    p = torch.as_tensor(params, dtype=torch.float64)
+    coef, *_ = tdamp._unpack(model, p)
+    a = tdamp.chain_amplitudes(model, torch.as_tensor(data), p)
+    s = (a * coef).abs().sum(dim=1)
+    y = float(p[-1])
+    gt = model.gamma * torch.as_tensor(t)
+    return (2 * torch.exp(-gt) * torch.cosh(y * gt) * s ** 2).numpy()
