@@ -52,11 +52,15 @@ struct tdmix_ctx {
   double* d_gram = nullptr;
   double* d_sumt = nullptr;
   int* d_floating = nullptr;
+  int* d_err = nullptr;  // timeout flag of bounded device waits
   double* h_params = nullptr;  // pinned
   double* h_result = nullptr;  // pinned
-  double* d_rows_mc = nullptr;
+  double* d_rows_mc = nullptr;    // column-major block partials, leading dimension ld_mc
   double* d_rows_data = nullptr;
   int rows_mc_cap = 0, rows_data_cap = 0;
+  int64_t ld_mc = 0, ld_data = 0;
+  double* d_colsum = nullptr;     // final-kernel column sums
+  unsigned* d_counter = nullptr;  // final-kernel block counter
   Sample data, mc;
   double sum_t = 0;
   std::vector<int> floating;
@@ -295,19 +299,23 @@ int prof_mark(tdmix_ctx* ctx, int c, int phase) {
   return TDMIX_OK;
 }
 
-int grid_for(tdmix_ctx* ctx, int64_t n, int bps) {
-  int64_t want = (n + kThreads - 1) / kThreads;
+int grid_for(tdmix_ctx* ctx, int64_t n, int bps, int threads = kThreads) {
+  int64_t want = (n + threads - 1) / threads;
   int64_t cap = int64_t(bps > 0 ? bps : 1) * ctx->num_sms;
   return int(want < cap ? want : cap);
 }
 
-int ensure_rows(tdmix_ctx* ctx, double** buf, int* cap, int rows, int width) {
-  if (rows * width <= *cap) return TDMIX_OK;
+// Partial buffer of `rows` rows (leading dimension) and `width` columns.
+int ensure_rows(tdmix_ctx* ctx, double** buf, int* cap, int64_t* ld, int rows, int width) {
+  if (rows <= *ld && rows * width <= *cap) return TDMIX_OK;
   if (*buf) cudaFree(*buf);
   *buf = nullptr;
   *cap = 0;
-  TDMIX_CK(cudaMalloc(buf, size_t(rows) * width * sizeof(double)));
-  *cap = rows * width;
+  *ld = 0;
+  const int r = rows > ctx->num_sms * 4 ? rows : ctx->num_sms * 4;
+  TDMIX_CK(cudaMalloc(buf, size_t(r) * width * sizeof(double)));
+  *cap = r * width;
+  *ld = r;
   return TDMIX_OK;
 }
 
@@ -346,27 +354,34 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   fa.want_grad = want_grad;
   fa.have_res_grad = full && want_grad;
   fa.result = ctx->d_result;
+  fa.err = ctx->d_err;
   if (full) {
     const int gmc = grid_for(ctx, ctx->mc.dev.n, ops->mc_blocks_per_sm(want_grad));
-    if ((rc = ensure_rows(ctx, &ctx->d_rows_mc, &ctx->rows_mc_cap, gmc, ops->mc_row_width))) return rc;
+    if ((rc = ensure_rows(ctx, &ctx->d_rows_mc, &ctx->rows_mc_cap, &ctx->ld_mc, gmc, ops->mc_row_width))) return rc;
     if ((rc = prof_mark(ctx, TDMIX_PROF_MC, 0))) return rc;
-    TDMIX_CK(ops->mc(want_grad, gmc, st, ctx->mc.dev, ctx->d_ec, ctx->d_rows_mc));
+    TDMIX_CK(ops->mc(want_grad, gmc, st, ctx->mc.dev, ctx->d_ec, ctx->d_rows_mc, ctx->ld_mc, ctx->d_err));
     if ((rc = prof_mark(ctx, TDMIX_PROF_MC, 1))) return rc;
-    fa.mc_rows = ctx->d_rows_mc;
+    fa.mc_part = ctx->d_rows_mc;
     fa.n_mc_rows = gmc;
+    fa.mc_ld = ctx->ld_mc;
   } else {
-    fa.mc_rows = nullptr;
+    fa.mc_part = nullptr;
     fa.n_mc_rows = 0;
+    fa.mc_ld = 0;
   }
-  const int gd = grid_for(ctx, ctx->data.dev.n, ops->data_blocks_per_sm(!full, want_grad));
-  if ((rc = ensure_rows(ctx, &ctx->d_rows_data, &ctx->rows_data_cap, gd, ops->data_row_width))) return rc;
+  const int gd = grid_for(ctx, ctx->data.dev.n, ops->data_blocks_per_sm(!full, want_grad), ops->data_threads);
+  if ((rc = ensure_rows(ctx, &ctx->d_rows_data, &ctx->rows_data_cap, &ctx->ld_data, gd, ops->data_row_width)))
+    return rc;
   if ((rc = prof_mark(ctx, TDMIX_PROF_DATA, 0))) return rc;
-  TDMIX_CK(ops->data(!full, want_grad, gd, st, ctx->data.dev, ctx->d_ec, ctx->d_rows_data, rates));
+  TDMIX_CK(ops->data(!full, want_grad, gd, st, ctx->data.dev, ctx->d_ec, ctx->d_rows_data, ctx->ld_data, rates));
   if ((rc = prof_mark(ctx, TDMIX_PROF_DATA, 1))) return rc;
-  fa.data_rows = ctx->d_rows_data;
+  fa.data_part = ctx->d_rows_data;
   fa.n_data_rows = gd;
+  fa.data_ld = ctx->ld_data;
+  fa.colsum = ctx->d_colsum;
+  fa.counter = ctx->d_counter;
   if ((rc = prof_mark(ctx, TDMIX_PROF_FINAL, 0))) return rc;
-  launch_final(fa, st);
+  launch_final(fa, ops->mc_row_width, ops->data_row_width, st);
   TDMIX_CK(cudaGetLastError());
   if ((rc = prof_mark(ctx, TDMIX_PROF_FINAL, 1))) return rc;
   if (full) {
@@ -382,9 +397,10 @@ int result_status(tdmix_ctx* ctx) {
   const double* r = ctx->h_result;
   if (r[2] < 0) {
     int st = int(r[2]);
-    return fail(ctx, st, st == TDMIX_ERR_DOMAIN ? "parameter outside its domain (|y| < 1, m0 > 0, Gamma0 > 0, "
-                                                  "pole above the decay threshold)"
-                                                : "non-finite parameter");
+    return fail(ctx, st, st == TDMIX_ERR_DOMAIN    ? "parameter outside its domain (|y| < 1, m0 > 0, Gamma0 > 0, "
+                                                       "pole above the decay threshold)"
+                         : st == TDMIX_ERR_TIMEOUT ? "a bounded device wait gave up (event tile copy did not arrive)"
+                                                   : "non-finite parameter");
   }
   if (r[2] > 0)
     return fail(ctx, TDMIX_ERR_NONFINITE, std::to_string(int64_t(r[2])) + " data events have a rate <= 0 or not finite");
@@ -427,6 +443,12 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   TDMIX_CK(cudaMalloc(&ctx->d_gram, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes) * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_sumt, sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_floating, np * sizeof(int)));
+  TDMIX_CK(cudaMalloc(&ctx->d_err, sizeof(int)));
+  TDMIX_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+  TDMIX_CK(cudaMalloc(&ctx->d_colsum, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes + 4 + 4 * kMaxComp + 2 * kMaxRes) *
+                                          sizeof(double)));
+  TDMIX_CK(cudaMalloc(&ctx->d_counter, sizeof(unsigned)));
+  TDMIX_CK(cudaMemset(ctx->d_counter, 0, sizeof(unsigned)));
   TDMIX_CK(cudaMallocHost(&ctx->h_params, np * sizeof(double)));
   TDMIX_CK(cudaMallocHost(&ctx->h_result, (kResHeader + np) * sizeof(double)));
   DevModel dm = make_dev_model(ctx->model);
@@ -599,6 +621,9 @@ void tdmix_destroy(tdmix_ctx* ctx) {
   cudaFree(ctx->d_gram);
   cudaFree(ctx->d_sumt);
   cudaFree(ctx->d_floating);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_colsum);
+  cudaFree(ctx->d_counter);
   cudaFree(ctx->d_rows_mc);
   cudaFree(ctx->d_rows_data);
   if (ctx->h_params) cudaFreeHost(ctx->h_params);

@@ -30,45 +30,40 @@ template <class S>
 struct Ops {
   static constexpr bool kOk = S::U <= kMaxRegisterGramU;
   static cudaError_t mc(bool grad, int grid, cudaStream_t st, const SampleDev& d, const EvalConst* ec,
-                        double* rows) {
+                        double* part, int64_t ld, int* err) {
     if constexpr (kOk) {
-      if (grad) k_mc<Prec, S, true><<<grid, 256, 0, st>>>(d, ec, rows);
-      else k_mc<Prec, S, false><<<grid, 256, 0, st>>>(d, ec, rows);
+      using T = typename Prec::T;
+      const bool weighted = d.w != nullptr;
+      const int smem = 2 * mc_planes<Prec, S>(weighted) * kMcTile * int(sizeof(T));
+      auto kern = grad ? (weighted ? k_mc<Prec, S, true, true> : k_mc<Prec, S, true, false>)
+                       : (weighted ? k_mc<Prec, S, false, true> : k_mc<Prec, S, false, false>);
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      kern<<<grid, kMcTile, smem, st>>>(d, ec, part, ld, err);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
   }
   static cudaError_t data(bool from_cache, bool grad, int grid, cudaStream_t st, const SampleDev& d,
-                          const EvalConst* ec, double* rows, double* rates) {
+                          const EvalConst* ec, double* part, int64_t ld, double* rates) {
     if constexpr (kOk) {
-      if (from_cache) {
-        if (grad) k_data<Prec, S, true, true><<<grid, 256, 0, st>>>(d, ec, rows, rates);
-        else k_data<Prec, S, true, false><<<grid, 256, 0, st>>>(d, ec, rows, rates);
-      } else {
-        if (grad) k_data<Prec, S, false, true><<<grid, 256, 0, st>>>(d, ec, rows, rates);
-        else k_data<Prec, S, false, false><<<grid, 256, 0, st>>>(d, ec, rows, rates);
-      }
+      auto kern = from_cache ? (grad ? k_data<Prec, S, true, true> : k_data<Prec, S, true, false>)
+                             : (grad ? k_data<Prec, S, false, true> : k_data<Prec, S, false, false>);
+      kern<<<grid, kDataThreads, 0, st>>>(d, ec, part, ld, rates);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
   }
-  static int mc_bps(bool grad) {
-    int n = 0;
-    if constexpr (kOk) {
-      if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mc<Prec, S, true>, 256, 0);
-      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mc<Prec, S, false>, 256, 0);
-    }
-    return n;
-  }
+  static int mc_bps(bool) { return 1; }  // persistent: one block per SM
   static int data_bps(bool from_cache, bool grad) {
     int n = 0;
     if constexpr (kOk) {
       if (from_cache) {
-        if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, true, true>, 256, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, true, false>, 256, 0);
+        if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, true, true>, kDataThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, true, false>, kDataThreads, 0);
       } else {
-        if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, false, true>, 256, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, false, false>, 256, 0);
+        if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, false, true>, kDataThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, false, false>, kDataThreads, 0);
       }
     }
     return n;
@@ -85,6 +80,7 @@ const ShapeOps* TDMIX_FIND(const std::string& sig) {
                                shapes::S::NR,                                                         \
                                1 + shapes::S::U * shapes::S::U + 2 * shapes::S::NR,                   \
                                4 + 4 * shapes::S::U + 2 * shapes::S::NR,                              \
+                               kDataThreads,                                                          \
                                &Ops<shapes::S>::mc,                                                   \
                                &Ops<shapes::S>::data,                                                 \
                                &Ops<shapes::S>::mc_bps,                                               \

@@ -205,46 +205,68 @@ void launch_prepare(const double* params, const DevModel* dm, EvalConst* ec, cud
 //   NLL = -sum ln B + Gamma sum t + N_d ln N,
 // and the gradient.  Result: [nll, N, n_bad, sum ln B, grad...].
 // ---------------------------------------------------------------------------
-constexpr int kFinalThreads = 1024;
+constexpr int kFinalThreads = 256;
+constexpr int kFinalColsPerBlock = kFinalThreads / 32;
 constexpr int kMaxMcWidth = 1 + kMaxComp * kMaxComp + 2 * kMaxRes;
 constexpr int kMaxDataWidth = 4 + 4 * kMaxComp + 2 * kMaxRes;
 
-// Column sums of a row-major [rows][width] array: warp w sums columns
-// w, w + 32, ...; lane l takes rows l, l + 32, ... in order, then a fixed
-// shuffle tree combines the lanes.
-__device__ inline void column_sums(const double* __restrict__ rows, int n_rows, int width, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int v = warp; v < width; v += nw) {
+// Final kernel, many blocks: warp c of the grid sums column c of the block
+// partials (MC columns first when an MC pass ran, then data columns); lane l
+// takes rows l, l + 32, ... in order and a fixed shuffle tree combines the
+// lanes.  The last block to finish (atomic counter) then forms
+//   N = <alpha |A|^2 + beta |Abar|^2 - 2 gc Re(A Abar*) - 2 dc Im(A Abar*)> / Gamma
+// (Eq. (mix) integrated over t in [0, inf), averaged over the MC sample),
+//   NLL = -sum ln B + Gamma sum t + N_d ln N,
+// and the gradient.  Result: [nll, N, n_bad or status, sum ln B, grad...].
+__global__ void __launch_bounds__(kFinalThreads) k_final(FinalArgs fa, int wmc, int wd) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nmc = fa.mc_part ? wmc : 0;
+  const int col = blockIdx.x * kFinalColsPerBlock + warp;
+  if (col < nmc + wd) {
+    const double* src;
+    int n;
+    if (col < nmc) {
+      src = fa.mc_part + int64_t(col) * fa.mc_ld;
+      n = fa.n_mc_rows;
+    } else {
+      src = fa.data_part + int64_t(col - nmc) * fa.data_ld;
+      n = fa.n_data_rows;
+    }
     double a = 0;
-    for (int r = lane; r < n_rows; r += 32) a += rows[size_t(r) * width + v];
+    for (int r = lane; r < n; r += 32) a += src[r];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
-    if (lane == 0) out[v] = a;
+    if (lane == 0) fa.colsum[col] = a;
   }
-}
+  __threadfence();
+  __syncthreads();
+  __shared__ unsigned last;
+  if (threadIdx.x == 0) last = atomicAdd(fa.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
 
-__global__ void __launch_bounds__(kFinalThreads) k_final(FinalArgs fa) {
   const DevModel* dm = fa.dm;
   const EvalConst* ec = fa.ec;
   const int U = dm->U, NR = dm->NR, nc = dm->n_chains, np = dm->n_params;
   const int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2;
-  const int wmc = 1 + NRE + NIM + 2 * NR;
-  const int wd = 4 + 4 * U + 2 * NR;
   const int tid = threadIdx.x;
   __shared__ double mcs[kMaxMcWidth];
   __shared__ double ds[kMaxDataWidth];
   __shared__ double Ire[kMaxComp * kMaxComp], Iim[kMaxComp * kMaxComp];
   __shared__ double vA[kMaxComp][2], vB[kMaxComp][2];
   __shared__ double sh[8];  // AA, BB, Xr, Xi, nbar
-  if (fa.mc_rows) {
-    column_sums(fa.mc_rows, fa.n_mc_rows, wmc, mcs);
-  } else {
-    for (int v = tid; v < wmc; v += blockDim.x) mcs[v] = fa.gram_store[v];
+  for (int v = tid; v < wmc; v += blockDim.x) {
+    if (fa.mc_part) {
+      mcs[v] = __ldcg(fa.colsum + v);
+      fa.gram_store[v] = mcs[v];
+    } else {
+      mcs[v] = fa.gram_store[v];
+    }
   }
-  column_sums(fa.data_rows, fa.n_data_rows, wd, ds);
+  for (int v = tid; v < wd; v += blockDim.x) ds[v] = __ldcg(fa.colsum + nmc + v);
+  if (tid == 0) *fa.counter = 0u;
   __syncthreads();
-  if (fa.mc_rows)
-    for (int v = tid; v < wmc; v += blockDim.x) fa.gram_store[v] = mcs[v];
   const double sw = mcs[0];
   for (int e = tid; e < U * U; e += blockDim.x) {
     const int j = e / U, k = e % U;
@@ -257,8 +279,12 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(FinalArgs fa) {
   }
   __syncthreads();
   double* res = fa.result;
-  if (ec->status != 0) {
-    for (int k = tid; k < kResHeader + np; k += blockDim.x) res[k] = k == 2 ? double(ec->status) : nan("");
+  const int timed_out = *fa.err;
+  const int status = timed_out ? -7 : ec->status;
+  __syncthreads();
+  if (tid == 0 && timed_out) *fa.err = 0;
+  if (status != 0) {
+    for (int k = tid; k < kResHeader + np; k += blockDim.x) res[k] = k == 2 ? double(status) : nan("");
     return;
   }
   // vA = I cA, vB = I cB (thread j)
@@ -301,6 +327,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(FinalArgs fa) {
   if (!fa.want_grad) return;
   const double AA = sh[0], BB = sh[1], Xr = sh[2], Xi = sh[3], nbar = sh[4];
   const double sc = Nd / nbar;  // d(N_d ln N) = N_d dnbar / nbar
+  // data columns: [sum ln B, n_bad, d/dx, d/dy, Re gA, Im gA, Re gB, Im gB, s1, s2]
   for (int c = tid; c < nc; c += blockDim.x) {
     const int j = dm->chain_comp[c];
     double dnr, dni, gr, gi;
@@ -347,6 +374,10 @@ __global__ void __launch_bounds__(kFinalThreads) k_final(FinalArgs fa) {
   }
 }
 
-void launch_final(const FinalArgs& fa, cudaStream_t st) { k_final<<<1, kFinalThreads, 0, st>>>(fa); }
+void launch_final(const FinalArgs& fa, int mc_width, int data_width, cudaStream_t st) {
+  const int cols = (fa.mc_part ? mc_width : 0) + data_width;
+  const int blocks = (cols + kFinalColsPerBlock - 1) / kFinalColsPerBlock;
+  k_final<<<blocks, kFinalThreads, 0, st>>>(fa, mc_width, data_width);
+}
 
 }  // namespace tdmix
