@@ -164,6 +164,42 @@ int tdmix_profile(tdmix_ctx* ctx, int enable);
  * totals afterwards. */
 int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, int reset);
 
+/* Allocation-free evaluation of sum_e ln B(e) (B from Eq. (mix) as above,
+ * without e^{-Gamma t}) over a component cache the caller keeps itself.
+ * The paper has no counterpart: this serves callers that cannot allocate
+ * device memory while they evaluate, such as work being recorded into a CUDA
+ * graph, code running under an external memory manager that owns every
+ * device allocation, or a latency-bound loop that must not wait on the
+ * allocator.  It calls no cudaMalloc/cudaFree and no allocating library
+ * routine: its block partial sums live in a file-scope device array of
+ * TDMIX_NOALLOC_MAX_BLOCKS * 2 doubles (16 KiB), which every GPU that loads
+ * the library holds until the process exits.
+ *   U            number of components, 1 .. 16
+ *   n, ld        events, and the plane stride (ld >= n) of a_re / a_im
+ *   a_re, a_im   device, [U][ld] doubles: real / imaginary part of a_j(e)
+ *   t            device, n decay times (ps)
+ *   cA, cB       device, 2U doubles each: coefficient of component j in A_f
+ *                and in Abar_f as interleaved (re, im)
+ *   x, y, gamma  mixing parameters and the D0 width (1/ps)
+ *   out          device, 2 doubles: [sum ln B over events with B > 0,
+ *                number of events with B <= 0 or not finite]
+ *   stream       cudaStream_t the work is enqueued on (asynchronous)
+ * Returns TDMIX_ERR_ARG for U outside 1..16, n < 1, ld < n or a null pointer
+ * (any n is accepted: blocks loop over events), TDMIX_ERR_DOMAIN for
+ * |y| >= 1 or gamma <= 0, TDMIX_ERR_CUDA if a launch fails.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture starts.
+ * Every call shares the array and leaves its partial sums there.  Each call
+ * writes every entry it later reads, so nothing needs clearing between
+ * calls; but two calls that overlap on the same GPU (for example enqueued on
+ * two streams with no ordering between them) race on the array, so such
+ * calls must be serialised by the caller. */
+#define TDMIX_NOALLOC_MAX_BLOCKS 1024
+#define TDMIX_NOALLOC_MAX_DEVICES 64
+int tdmix_loglik_components_noalloc(int U, int64_t n, const double* a_re, const double* a_im, int64_t ld,
+                                    const double* t, const double* cA, const double* cB, double x, double y,
+                                    double gamma, double* out, void* stream);
+
 /* Text of the last failure of this context (never NULL). */
 const char* tdmix_last_error(const tdmix_ctx* ctx);
 

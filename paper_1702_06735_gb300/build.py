@@ -61,6 +61,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         ("eval_inst.cu", "eval_f64.o", ["-DTDMIX_PREC_F32=0"]),
         ("eval_inst.cu", "eval_f32.o", ["-DTDMIX_PREC_F32=1"]),
         ("capi.cu", "capi.o", []),
+        ("noalloc.cu", "noalloc.o", []),
         ("model.cpp", "model.o", []),
         ("json.cpp", "json.o", []),
     ]

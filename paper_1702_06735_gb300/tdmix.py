@@ -39,6 +39,8 @@ _SIGNATURES = {
     "tdmix_norm_matrix": (_c_i, [_c_p, _c_p]),
     "tdmix_profile": (_c_i, [_c_p, _c_i]),
     "tdmix_profile_read": (_c_i, [_c_p, _c_p, _c_p, _c_i]),
+    "tdmix_loglik_components_noalloc": (_c_i, [_c_i, ctypes.c_int64, _c_p, _c_p, ctypes.c_int64, _c_p, _c_p, _c_p,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, _c_p, _c_p]),
     "tdmix_last_error": (ctypes.c_char_p, [_c_p]),
     "tdmix_destroy": (None, [_c_p]),
 }
