@@ -327,13 +327,16 @@ def run_tdmix(args):
     if rank != 0:
         return 0
 
-    # roofline of the dominant kernel (the MC pass): algorithmic bytes per MC
-    # event = invariants (hi+lo fp32) + width factors + spin x barrier factors
-    NS, NX, NT = 7, 4, 16
-    bytes_per_event = NS * 8 + NX * 4 + NT * 4
-    mc_ms, mc_n = prof32["mc"]
-    mc_launch_ms = mc_ms / mc_n
-    achieved = bytes_per_event * N_MC / (mc_launch_ms * 1e-3) / 1e9
+    # roofline of the evaluation kernel (the only kernel of a step): algorithmic
+    # bytes = per MC event the invariants (hi+lo fp32), width factors and spin x
+    # barrier factors; per data event the same planes, its decay time (f64)
+    # and the component cache written back (U complex fp32)
+    NS, NX, NT, U = 7, 4, 16, 8
+    plane_bytes = NS * 8 + NX * 4 + NT * 4
+    bytes_per_launch = N_MC * plane_bytes + N_DATA * (plane_bytes + 8 + 2 * U * 4)
+    ev_ms, ev_n = prof32["eval"]
+    ev_launch_ms = ev_ms / ev_n
+    achieved = bytes_per_launch / (ev_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     launches = sum(n for _, n in prof32.values())
     np_ = len(p0)
@@ -361,9 +364,10 @@ def run_tdmix(args):
         "fixed_model_xy_only": {"value": nfix / fixed_s, "unit": "evals/s",
                                 "note": "host-buffer calls reusing the component cache and stored normalisation matrix"},
         "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof32.items()},
-        "roofline": {"kernel": "k_mc (MC pass, fp32 path)", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-                     "algorithmic_bytes_per_launch": bytes_per_event * N_MC},
+        "roofline": {"kernel": "k_eval (one full evaluation, fp32 path)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "launch_ms": ev_launch_ms},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 8 * np_,
                 "d2h_bytes_per_step": 8 * (4 + np_)},
         "gpu_launches": launches,

@@ -146,11 +146,11 @@ int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
 
 /* Kernel classes timed by tdmix_profile. */
 enum {
-  TDMIX_PROF_PREPARE = 0, /* per-evaluation constants from the parameters */
-  TDMIX_PROF_MC = 1,      /* MC pass: lineshapes, components, normalisation matrix, adjoint */
-  TDMIX_PROF_DATA = 2,    /* data pass: components (or cache), Eq. (mix), log sum, adjoint */
-  TDMIX_PROF_FINAL = 3,   /* fixed-order reduction, normalisation, NLL and gradient */
-  TDMIX_PROF_CLASSES = 4
+  TDMIX_PROF_EVAL = 0,       /* one evaluation: per-evaluation constants, data tiles (components or
+                                cache, Eq. (mix), log sum, adjoint), MC tiles (components,
+                                normalisation matrix, adjoint), fixed-order reduction, N, NLL, gradient */
+  TDMIX_PROF_PRECOMPUTE = 1, /* once per event load: invariants, width and spin x barrier factors */
+  TDMIX_PROF_CLASSES = 2
 };
 
 /* Enables (1) or disables (0) timing of every kernel the context launches:
@@ -163,6 +163,19 @@ int tdmix_profile(tdmix_ctx* ctx, int enable);
  * last reset; synchronises with the recorded events.  reset != 0 clears the
  * totals afterwards. */
 int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, int reset);
+
+/* Tracing (library extension for measurement; the paper has no
+ * counterpart).  With tracing on, every block of the evaluation kernel
+ * records TDMIX_TRACE_PHASES globaltimer stamps (ns): start, per-evaluation
+ * constants ready, data tiles done, MC tiles done, partials written, then
+ * in the last block only: column totals formed, NLL written, end (other
+ * blocks repeat their "partials written" stamp there).  Unused rows stay 0. */
+#define TDMIX_TRACE_PHASES 8
+int tdmix_trace(tdmix_ctx* ctx, int enable);
+/* Stamps of the last evaluation: stamps[block * TDMIX_TRACE_PHASES + phase]
+ * for *n_blocks blocks (host array of at least (number of SMs) *
+ * TDMIX_TRACE_PHASES entries); synchronises with the context's stream. */
+int tdmix_trace_read(tdmix_ctx* ctx, unsigned long long* stamps, int* n_blocks);
 
 /* Allocation-free evaluation of sum_e ln B(e) (B from Eq. (mix) as above,
  * without e^{-Gamma t}) over a component cache the caller keeps itself.

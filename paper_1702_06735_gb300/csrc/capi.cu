@@ -46,23 +46,22 @@ struct tdmix_ctx {
   cudaStream_t stream = nullptr;
   int device = 0, num_sms = 0;
   DevModel* d_model = nullptr;
-  EvalConst* d_ec = nullptr;
   double* d_params = nullptr;
   double* d_result = nullptr;
   double* d_gram = nullptr;
   double* d_sumt = nullptr;
   int* d_floating = nullptr;
   int* d_err = nullptr;  // timeout flag of bounded device waits
+  unsigned long long* d_trace = nullptr;  // per-block phase stamps of the last evaluation (tracing on)
+  int64_t* d_ranges = nullptr;            // per-block MC tile ranges [num_sms + 1]
+  int64_t ranges_key[3] = {-1, -1, -1};   // (data tiles, MC tiles, grid) the ranges were made for
   double* h_params = nullptr;  // pinned
   double* h_result = nullptr;  // pinned
-  double* d_rows_mc = nullptr;    // column-major block partials, leading dimension ld_mc
-  double* d_rows_data = nullptr;
-  int rows_mc_cap = 0, rows_data_cap = 0;
-  int64_t ld_mc = 0, ld_data = 0;
-  double* d_colsum = nullptr;     // final-kernel column sums
-  unsigned* d_counter = nullptr;  // final-kernel block counter
+  void* d_part = nullptr;         // block partials of the evaluation kernel (float2 [width][num_sms])
+  unsigned* d_counter = nullptr;  // blocks finished (returned to 0 by the kernel)
   Sample data, mc;
   double sum_t = 0;
+  double inv_sum_w = 1.0;  // 1 / sum of MC weights
   std::vector<int> floating;
   std::vector<double> last_res;
   bool cache_valid = false, gram_valid = false;
@@ -70,9 +69,9 @@ struct tdmix_ctx {
   // kernel profiling: CUDA event pairs per kernel class, recorded on the stream
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev[TDMIX_PROF_CLASSES][2];
-  int prof_used[TDMIX_PROF_CLASSES] = {0, 0, 0, 0};
-  double prof_ms[TDMIX_PROF_CLASSES] = {0, 0, 0, 0};
-  int64_t prof_n[TDMIX_PROF_CLASSES] = {0, 0, 0, 0};
+  int prof_used[TDMIX_PROF_CLASSES] = {};
+  double prof_ms[TDMIX_PROF_CLASSES] = {};
+  int64_t prof_n[TDMIX_PROF_CLASSES] = {};
 };
 
 namespace {
@@ -164,6 +163,36 @@ int check_params(tdmix_ctx* ctx, const double* p) {
   return TDMIX_OK;
 }
 
+constexpr int kProfPool = 4096;
+
+// Folds recorded event pairs into the accumulated times (synchronises).
+int prof_drain(tdmix_ctx* ctx) {
+  for (int c = 0; c < TDMIX_PROF_CLASSES; ++c) {
+    for (int k = 0; k < ctx->prof_used[c]; ++k) {
+      float ms = 0;
+      TDMIX_CK(cudaEventSynchronize(ctx->prof_ev[c][1][k]));
+      TDMIX_CK(cudaEventElapsedTime(&ms, ctx->prof_ev[c][0][k], ctx->prof_ev[c][1][k]));
+      ctx->prof_ms[c] += ms;
+      ctx->prof_n[c] += 1;
+    }
+    ctx->prof_used[c] = 0;
+  }
+  return TDMIX_OK;
+}
+
+// Records the start (phase 0) or end (phase 1) of a kernel of class c.
+int prof_mark(tdmix_ctx* ctx, int c, int phase) {
+  if (!ctx->prof_on) return TDMIX_OK;
+  if (phase == 0 && ctx->prof_used[c] == kProfPool) {
+    int rc = prof_drain(ctx);
+    if (rc) return rc;
+  }
+  const int k = ctx->prof_used[c];
+  TDMIX_CK(cudaEventRecord(ctx->prof_ev[c][phase][k], ctx->stream));
+  if (phase == 1) ctx->prof_used[c] = k + 1;
+  return TDMIX_OK;
+}
+
 int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s) {
   const CompiledModel& m = ctx->model;
   if (ev->n < 1) return fail(ctx, TDMIX_ERR_ARG, "an event sample needs n >= 1");
@@ -252,9 +281,33 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
     if (ctx->f32) launch_to_f32(wsrc, static_cast<float*>(w), n, st);
     else cudaMemcpyAsync(w, wsrc, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     d.w = w;
+    double sw = 0;
+    launch_sum(wsrc, n, ctx->d_sumt, st);
+    cudaMemcpyAsync(&sw, ctx->d_sumt, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || !(sw > 0)) {
+      cleanup();
+      free_sample(s);
+      return fail(ctx, TDMIX_ERR_ARG, "MC weights must have a positive sum");
+    }
+    ctx->inv_sum_w = 1.0 / sw;
+  } else if (!is_data) {
+    ctx->inv_sum_w = 1.0 / double(n);
+  }
+  int prc = prof_mark(ctx, TDMIX_PROF_PRECOMPUTE, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cleanup();
+    free_sample(s);
+    return fail(ctx, TDMIX_ERR_CUDA, std::string("before precompute: ") + cudaGetErrorString(e));
   }
   launch_precompute(ctx->f32, mom, n, pitch, ctx->d_model, d.s, d.x, d.k, st);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
+  if (!prc) prc = prof_mark(ctx, TDMIX_PROF_PRECOMPUTE, 1);
+  if (prc) {
+    cleanup();
+    free_sample(s);
+    return prc;
+  }
   if (e == cudaSuccess && is_data) {
     launch_sum(d.t, n, ctx->d_sumt, st);
     e = cudaMemcpyAsync(&ctx->sum_t, ctx->d_sumt, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -266,56 +319,6 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
     return fail(ctx, TDMIX_ERR_CUDA, std::string("precompute: ") + cudaGetErrorString(e));
   }
   s.loaded = true;
-  return TDMIX_OK;
-}
-
-constexpr int kProfPool = 4096;
-
-// Folds recorded event pairs into the accumulated times (synchronises).
-int prof_drain(tdmix_ctx* ctx) {
-  for (int c = 0; c < TDMIX_PROF_CLASSES; ++c) {
-    for (int k = 0; k < ctx->prof_used[c]; ++k) {
-      float ms = 0;
-      TDMIX_CK(cudaEventSynchronize(ctx->prof_ev[c][1][k]));
-      TDMIX_CK(cudaEventElapsedTime(&ms, ctx->prof_ev[c][0][k], ctx->prof_ev[c][1][k]));
-      ctx->prof_ms[c] += ms;
-      ctx->prof_n[c] += 1;
-    }
-    ctx->prof_used[c] = 0;
-  }
-  return TDMIX_OK;
-}
-
-// Records the start (phase 0) or end (phase 1) of a kernel of class c.
-int prof_mark(tdmix_ctx* ctx, int c, int phase) {
-  if (!ctx->prof_on) return TDMIX_OK;
-  if (phase == 0 && ctx->prof_used[c] == kProfPool) {
-    int rc = prof_drain(ctx);
-    if (rc) return rc;
-  }
-  const int k = ctx->prof_used[c];
-  TDMIX_CK(cudaEventRecord(ctx->prof_ev[c][phase][k], ctx->stream));
-  if (phase == 1) ctx->prof_used[c] = k + 1;
-  return TDMIX_OK;
-}
-
-int grid_for(tdmix_ctx* ctx, int64_t n, int bps, int threads = kThreads) {
-  int64_t want = (n + threads - 1) / threads;
-  int64_t cap = int64_t(bps > 0 ? bps : 1) * ctx->num_sms;
-  return int(want < cap ? want : cap);
-}
-
-// Partial buffer of `rows` rows (leading dimension) and `width` columns.
-int ensure_rows(tdmix_ctx* ctx, double** buf, int* cap, int64_t* ld, int rows, int width) {
-  if (rows <= *ld && rows * width <= *cap) return TDMIX_OK;
-  if (*buf) cudaFree(*buf);
-  *buf = nullptr;
-  *cap = 0;
-  *ld = 0;
-  const int r = rows > ctx->num_sms * 4 ? rows : ctx->num_sms * 4;
-  TDMIX_CK(cudaMalloc(buf, size_t(r) * width * sizeof(double)));
-  *cap = r * width;
-  *ld = r;
   return TDMIX_OK;
 }
 
@@ -339,51 +342,51 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
     TDMIX_CK(cudaMemcpyAsync(ctx->d_params, params, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   int rc;
-  if ((rc = prof_mark(ctx, TDMIX_PROF_PREPARE, 0))) return rc;
-  launch_prepare(ctx->d_params, ctx->d_model, ctx->d_ec, st);
-  TDMIX_CK(cudaGetLastError());
-  if ((rc = prof_mark(ctx, TDMIX_PROF_PREPARE, 1))) return rc;
-  const ShapeOps* ops = ctx->ops;
-  FinalArgs fa{};
-  fa.dm = ctx->d_model;
-  fa.ec = ctx->d_ec;
-  fa.gram_store = ctx->d_gram;
-  fa.n_data = ctx->data.dev.n;
-  fa.sum_t = ctx->sum_t;
-  fa.floating = ctx->d_floating;
-  fa.want_grad = want_grad;
-  fa.have_res_grad = full && want_grad;
-  fa.result = ctx->d_result;
-  fa.err = ctx->d_err;
+  const int64_t items = (ctx->data.dev.n + 255) / 256 + (full ? (ctx->mc.dev.n + 255) / 256 : 0);
+  const int grid = int(items < ctx->num_sms ? items : ctx->num_sms);
+  EvalArgs a{};
+  a.data = ctx->data.dev;
+  a.mc = ctx->mc.dev;
+  a.params = ctx->d_params;
+  a.dm = ctx->d_model;
+  a.part = ctx->d_part;
+  a.ld = ctx->num_sms;
+  a.gram_store = ctx->d_gram;
+  a.counter = ctx->d_counter;
+  a.err = ctx->d_err;
+  a.rates = rates;
+  a.result = ctx->d_result;
+  a.sum_t = ctx->sum_t;
+  a.inv_sum_w = ctx->inv_sum_w;
+  a.trace = ctx->d_trace;
   if (full) {
-    const int gmc = grid_for(ctx, ctx->mc.dev.n, ops->mc_blocks_per_sm(want_grad));
-    if ((rc = ensure_rows(ctx, &ctx->d_rows_mc, &ctx->rows_mc_cap, &ctx->ld_mc, gmc, ops->mc_row_width))) return rc;
-    if ((rc = prof_mark(ctx, TDMIX_PROF_MC, 0))) return rc;
-    TDMIX_CK(ops->mc(want_grad, gmc, st, ctx->mc.dev, ctx->d_ec, ctx->d_rows_mc, ctx->ld_mc, ctx->d_err));
-    if ((rc = prof_mark(ctx, TDMIX_PROF_MC, 1))) return rc;
-    fa.mc_part = ctx->d_rows_mc;
-    fa.n_mc_rows = gmc;
-    fa.mc_ld = ctx->ld_mc;
-  } else {
-    fa.mc_part = nullptr;
-    fa.n_mc_rows = 0;
-    fa.mc_ld = 0;
+    // Static, cost-balanced assignment of MC tiles to blocks: block q takes
+    // data tiles q, q + grid, ... and MC tiles [range[q], range[q + 1]).
+    const int64_t n_dt = (ctx->data.dev.n + 255) / 256, n_mt = (ctx->mc.dev.n + 255) / 256;
+    if (ctx->ranges_key[0] != n_dt || ctx->ranges_key[1] != n_mt || ctx->ranges_key[2] != grid) {
+      const int64_t R = ctx->f32 ? kDataTileCostF32 : kDataTileCostF64;
+      const int64_t total = R * n_dt + n_mt, G = grid;
+      std::vector<int64_t> rg(G + 1, 0);
+      int64_t run = 0, data_upto = 0;
+      for (int64_t q = 0; q < G; ++q) {
+        data_upto += n_dt > q ? (n_dt - 1 - q) / G + 1 : 0;  // data tiles of blocks <= q
+        int64_t e = (q + 1) * total / G - R * data_upto;
+        e = e < 0 ? 0 : (e > n_mt ? n_mt : e);
+        run = e > run ? e : run;
+        rg[q + 1] = q == G - 1 ? n_mt : run;
+      }
+      TDMIX_CK(cudaMemcpyAsync(ctx->d_ranges, rg.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+      TDMIX_CK(cudaStreamSynchronize(st));
+      ctx->ranges_key[0] = n_dt;
+      ctx->ranges_key[1] = n_mt;
+      ctx->ranges_key[2] = grid;
+    }
   }
-  const int gd = grid_for(ctx, ctx->data.dev.n, ops->data_blocks_per_sm(!full, want_grad), ops->data_threads);
-  if ((rc = ensure_rows(ctx, &ctx->d_rows_data, &ctx->rows_data_cap, &ctx->ld_data, gd, ops->data_row_width)))
-    return rc;
-  if ((rc = prof_mark(ctx, TDMIX_PROF_DATA, 0))) return rc;
-  TDMIX_CK(ops->data(!full, want_grad, gd, st, ctx->data.dev, ctx->d_ec, ctx->d_rows_data, ctx->ld_data, rates));
-  if ((rc = prof_mark(ctx, TDMIX_PROF_DATA, 1))) return rc;
-  fa.data_part = ctx->d_rows_data;
-  fa.n_data_rows = gd;
-  fa.data_ld = ctx->ld_data;
-  fa.colsum = ctx->d_colsum;
-  fa.counter = ctx->d_counter;
-  if ((rc = prof_mark(ctx, TDMIX_PROF_FINAL, 0))) return rc;
-  launch_final(fa, ops->mc_row_width, ops->data_row_width, st);
-  TDMIX_CK(cudaGetLastError());
-  if ((rc = prof_mark(ctx, TDMIX_PROF_FINAL, 1))) return rc;
+  a.mc_ranges = ctx->d_ranges;
+
+  if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
+  TDMIX_CK(ctx->ops->eval(full, want_grad, grid, st, a, ctx->d_floating));
+  if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 1))) return rc;
   if (full) {
     ctx->gram_valid = true;
     ctx->cache_valid = true;
@@ -437,7 +440,6 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   TDMIX_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
   const int np = ctx->model.n_params();
   TDMIX_CK(cudaMalloc(&ctx->d_model, sizeof(DevModel)));
-  TDMIX_CK(cudaMalloc(&ctx->d_ec, sizeof(EvalConst)));
   TDMIX_CK(cudaMalloc(&ctx->d_params, np * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_result, (kResHeader + np) * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_gram, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes) * sizeof(double)));
@@ -445,9 +447,9 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   TDMIX_CK(cudaMalloc(&ctx->d_floating, np * sizeof(int)));
   TDMIX_CK(cudaMalloc(&ctx->d_err, sizeof(int)));
   TDMIX_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
-  TDMIX_CK(cudaMalloc(&ctx->d_colsum, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes + 4 + 4 * kMaxComp + 2 * kMaxRes) *
-                                          sizeof(double)));
+  TDMIX_CK(cudaMalloc(&ctx->d_part, size_t(ctx->num_sms) * (ctx->ops->mc_width + ctx->ops->data_width) * 8));
   TDMIX_CK(cudaMalloc(&ctx->d_counter, sizeof(unsigned)));
+  TDMIX_CK(cudaMalloc(&ctx->d_ranges, (ctx->num_sms + 1) * sizeof(int64_t)));
   TDMIX_CK(cudaMemset(ctx->d_counter, 0, sizeof(unsigned)));
   TDMIX_CK(cudaMallocHost(&ctx->h_params, np * sizeof(double)));
   TDMIX_CK(cudaMallocHost(&ctx->h_result, (kResHeader + np) * sizeof(double)));
@@ -491,6 +493,7 @@ int tdmix_set_floating(tdmix_ctx* ctx, const int* mask) {
 
 int tdmix_load_events(tdmix_ctx* ctx, const tdmix_events* data, const tdmix_events* mc) {
   if (!ctx) return TDMIX_ERR_ARG;
+  cudaGetLastError();  // a failure left by earlier, unrelated work must not be reported here
   if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
   int rc;
   if (data && (rc = load_sample(ctx, data, true, ctx->data))) return rc;
@@ -503,6 +506,7 @@ int tdmix_load_events(tdmix_ctx* ctx, const tdmix_events* data, const tdmix_even
 int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* grad_out) {
   if (!ctx || !params || !nll_out) return fail(ctx, TDMIX_ERR_ARG, "null argument");
   if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  cudaGetLastError();  // a failure left by earlier, unrelated work must not be reported here
   const bool host_params = !is_device_ptr(params);
   const bool host_out = !is_device_ptr(nll_out);
   if (grad_out && is_device_ptr(grad_out) == host_out)
@@ -604,6 +608,30 @@ int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, in
   return TDMIX_OK;
 }
 
+int tdmix_trace(tdmix_ctx* ctx, int enable) {
+  if (!ctx) return TDMIX_ERR_ARG;
+  if (enable && !ctx->d_trace) {
+    TDMIX_CK(cudaMalloc(&ctx->d_trace, size_t(ctx->num_sms) * kTracePhases * sizeof(unsigned long long)));
+    TDMIX_CK(cudaMemset(ctx->d_trace, 0, size_t(ctx->num_sms) * kTracePhases * sizeof(unsigned long long)));
+  } else if (!enable && ctx->d_trace) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_trace);
+  cudaFree(ctx->d_ranges);
+    ctx->d_trace = nullptr;
+  }
+  return TDMIX_OK;
+}
+
+int tdmix_trace_read(tdmix_ctx* ctx, unsigned long long* stamps, int* n_blocks) {
+  if (!ctx || !stamps || !n_blocks) return fail(ctx, TDMIX_ERR_ARG, "null argument");
+  if (!ctx->d_trace) return fail(ctx, TDMIX_ERR_STATE, "tracing is off");
+  TDMIX_CK(cudaStreamSynchronize(ctx->stream));
+  TDMIX_CK(cudaMemcpy(stamps, ctx->d_trace, size_t(ctx->num_sms) * kTracePhases * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+  *n_blocks = ctx->num_sms;
+  return TDMIX_OK;
+}
+
 const char* tdmix_last_error(const tdmix_ctx* ctx) {
   if (!ctx) return "null context";
   return ctx->err.c_str();
@@ -615,17 +643,16 @@ void tdmix_destroy(tdmix_ctx* ctx) {
   free_sample(ctx->data);
   free_sample(ctx->mc);
   cudaFree(ctx->d_model);
-  cudaFree(ctx->d_ec);
   cudaFree(ctx->d_params);
   cudaFree(ctx->d_result);
   cudaFree(ctx->d_gram);
   cudaFree(ctx->d_sumt);
   cudaFree(ctx->d_floating);
   cudaFree(ctx->d_err);
-  cudaFree(ctx->d_colsum);
   cudaFree(ctx->d_counter);
-  cudaFree(ctx->d_rows_mc);
-  cudaFree(ctx->d_rows_data);
+  cudaFree(ctx->d_part);
+  cudaFree(ctx->d_trace);
+  cudaFree(ctx->d_ranges);
   if (ctx->h_params) cudaFreeHost(ctx->h_params);
   if (ctx->h_result) cudaFreeHost(ctx->h_result);
   for (int c = 0; c < TDMIX_PROF_CLASSES; ++c)

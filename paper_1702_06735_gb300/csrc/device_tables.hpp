@@ -23,20 +23,6 @@ struct DevModel {
   double xplane_ma[kMaxXPlanes], xplane_mb[kMaxXPlanes];
 };
 
-// Per-evaluation constants derived from the parameter vector on the device.
-struct EvalConst {
-  double m0[kMaxRes], g0[kMaxRes], m2[kMaxRes];
-  double kappa[kMaxRes];     // m0 Gamma(s) = kappa * X(s)
-  double dk_dm[kMaxRes], dk_dg[kMaxRes];
-  float m2_hi[kMaxRes], m2_lo[kMaxRes], kappa_f[kMaxRes];
-  double cA[kMaxComp][2], cB[kMaxComp][2];   // coefficient of each component in A_f, Abar_f
-  float cAf[kMaxComp][2], cBf[kMaxComp][2];
-  double x, y, gamma;
-  double alpha, beta, gc, dc;                 // time-integral weights of |A|^2, |Abar|^2, Re, Im
-  float alpha_f, beta_f, gc_f, dc_f;
-  int status;                                 // tdmix_status of the parameter check
-};
-
 // Device view of one event sample (data or phase-space MC).
 struct SampleDev {
   int64_t n, pitch;
@@ -48,25 +34,35 @@ struct SampleDev {
   void* cache;        // per-event components [2][U][pitch] (data)
 };
 
-// Layout of one block-partial row.
-struct RowLayout {
-  // MC rows
-  static constexpr int mc_sumw = 0;
-  static int mc_gre(int U) { return 1; }                 // U*U, upper triangle used
-  static int mc_gim(int U) { return 1 + U * U; }
-  static int mc_s1(int U) { return 1 + 2 * U * U; }
-  static int mc_s2(int U, int NR) { return 1 + 2 * U * U + NR; }
-  static int mc_width(int U, int NR) { return 1 + 2 * U * U + 2 * NR; }
-  // data rows
-  static constexpr int d_lnb = 0, d_bad = 1, d_gx = 2, d_gy = 3;
-  static int d_ga(int U) { return 4; }                    // [re U][im U]
-  static int d_gb(int U) { return 4 + 2 * U; }
-  static int d_s1(int U) { return 4 + 4 * U; }
-  static int d_s2(int U, int NR) { return 4 + 4 * U + NR; }
-  static int d_width(int U, int NR) { return 4 + 4 * U + 2 * NR; }
+// Arguments of the fused evaluation kernel.
+struct EvalArgs {
+  SampleDev data, mc;
+  const double* params;
+  const DevModel* dm;
+  void* part;            // float2 [width][ld] double-float block partials (MC columns, then data columns)
+  int64_t ld;            // leading dimension of part (>= grid)
+  double* gram_store;    // MC column totals of the last pass that ran the MC tiles
+  unsigned* counter;     // blocks finished; returned to 0 by the last block
+  int* err;              // bounded-wait failures; read and cleared by the last block
+  double* rates;         // optional: e^{-Gamma t} B per data event
+  double* result;        // [nll, N, n_bad or status, sum ln B, grad...]
+  double sum_t;
+  double inv_sum_w;           // 1 / sum of MC weights (the MC event count when unweighted)
+  unsigned long long* trace;  // optional: per block kTracePhases globaltimer stamps (ns)
+  const int64_t* mc_ranges;   // [grid + 1]: block b takes MC tiles [mc_ranges[b], mc_ranges[b + 1])
 };
 
-// Result vector written by the final kernel: [nll, N, n_bad, sum ln B, grad...]
+// Phases stamped by the evaluation kernel when tracing is on: start,
+// constants ready, data tiles done, MC tiles done, partials written, and in
+// the last block: column totals formed, result written; end.
+constexpr int kTracePhases = 8;
+
+// Relative cost of one data tile in units of one MC tile (used to balance
+// the static assignment of tiles to blocks).
+constexpr int kDataTileCostF32 = 4;
+constexpr int kDataTileCostF64 = 1;
+
+// Result vector written by the evaluation kernel: [nll, N, n_bad or status, sum ln B, grad...]
 constexpr int kResHeader = 4;
 
 }  // namespace tdmix

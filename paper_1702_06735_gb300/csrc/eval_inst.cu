@@ -2,7 +2,7 @@
 // one precision (TDMIX_PREC_F32 = 0: fp64 path, 1: fp32 precision path).
 #include <string>
 
-#include "eval.cuh"
+#include "fused.cuh"
 #include "kernels.hpp"
 #include "shapes_gen.h"
 
@@ -29,63 +29,41 @@ constexpr int kMaxRegisterGramU = 8;
 template <class S>
 struct Ops {
   static constexpr bool kOk = S::U <= kMaxRegisterGramU;
-  static cudaError_t mc(bool grad, int grid, cudaStream_t st, const SampleDev& d, const EvalConst* ec,
-                        double* part, int64_t ld, int* err) {
-    if constexpr (kOk) {
-      using T = typename Prec::T;
-      const bool weighted = d.w != nullptr;
-      const int smem = 2 * mc_planes<Prec, S>(weighted) * kMcTile * int(sizeof(T));
-      auto kern = grad ? (weighted ? k_mc<Prec, S, true, true> : k_mc<Prec, S, true, false>)
-                       : (weighted ? k_mc<Prec, S, false, true> : k_mc<Prec, S, false, false>);
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  template <bool FULL, bool GRAD, bool W>
+  static cudaError_t launch(int grid, cudaStream_t st, const EvalArgs& a, const int* floating) {
+    const int smem = Layout<Prec, S>::smem_bytes(FULL, int(a.ld));
+    static int attr_set = 0;  // per instantiation: the largest size allowed so far
+    if (smem > attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_eval<Prec, S, FULL, GRAD, W>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
-      kern<<<grid, kMcTile, smem, st>>>(d, ec, part, ld, err);
-      return cudaGetLastError();
+      attr_set = smem;
     }
-    return cudaErrorNotSupported;
+    k_eval<Prec, S, FULL, GRAD, W><<<grid, kTile, smem, st>>>(a, floating);
+    return cudaGetLastError();
   }
-  static cudaError_t data(bool from_cache, bool grad, int grid, cudaStream_t st, const SampleDev& d,
-                          const EvalConst* ec, double* part, int64_t ld, double* rates) {
+  static cudaError_t eval(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a, const int* floating) {
     if constexpr (kOk) {
-      auto kern = from_cache ? (grad ? k_data<Prec, S, true, true> : k_data<Prec, S, true, false>)
-                             : (grad ? k_data<Prec, S, false, true> : k_data<Prec, S, false, false>);
-      kern<<<grid, kDataThreads, 0, st>>>(d, ec, part, ld, rates);
-      return cudaGetLastError();
-    }
-    return cudaErrorNotSupported;
-  }
-  static int mc_bps(bool) { return 1; }  // persistent: one block per SM
-  static int data_bps(bool from_cache, bool grad) {
-    int n = 0;
-    if constexpr (kOk) {
-      if (from_cache) {
-        if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, true, true>, kDataThreads, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, true, false>, kDataThreads, 0);
-      } else {
-        if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, false, true>, kDataThreads, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_data<Prec, S, false, false>, kDataThreads, 0);
+      const bool w = a.mc.w != nullptr;
+      if (full) {
+        if (grad) return w ? launch<true, true, true>(grid, st, a, floating) : launch<true, true, false>(grid, st, a, floating);
+        return w ? launch<true, false, true>(grid, st, a, floating) : launch<true, false, false>(grid, st, a, floating);
       }
+      return grad ? launch<false, true, false>(grid, st, a, floating) : launch<false, false, false>(grid, st, a, floating);
     }
-    return n;
+    return cudaErrorNotSupported;
   }
 };
 
 }  // namespace
 
 const ShapeOps* TDMIX_FIND(const std::string& sig) {
-#define TDMIX_SHAPE_ENTRY(S)                                                                          \
-  if (Ops<shapes::S>::kOk && sig == shapes::S::sig()) {                                               \
-    static const ShapeOps o = {shapes::S::sig(),                                                      \
-                               shapes::S::U,                                                          \
-                               shapes::S::NR,                                                         \
-                               1 + shapes::S::U * shapes::S::U + 2 * shapes::S::NR,                   \
-                               4 + 4 * shapes::S::U + 2 * shapes::S::NR,                              \
-                               kDataThreads,                                                          \
-                               &Ops<shapes::S>::mc,                                                   \
-                               &Ops<shapes::S>::data,                                                 \
-                               &Ops<shapes::S>::mc_bps,                                               \
-                               &Ops<shapes::S>::data_bps};                                            \
-    return &o;                                                                                        \
+#define TDMIX_SHAPE_ENTRY(S)                                                                  \
+  if (Ops<shapes::S>::kOk && sig == shapes::S::sig()) {                                       \
+    static const ShapeOps o = {shapes::S::sig(), shapes::S::U, shapes::S::NR,                 \
+                               Layout<Prec, shapes::S>::WMC, Layout<Prec, shapes::S>::WD,     \
+                               &Ops<shapes::S>::eval};                                        \
+    return &o;                                                                                \
   }
   TDMIX_FOR_EACH_SHAPE(TDMIX_SHAPE_ENTRY)
 #undef TDMIX_SHAPE_ENTRY

@@ -41,6 +41,8 @@ _SIGNATURES = {
     "tdmix_profile_read": (_c_i, [_c_p, _c_p, _c_p, _c_i]),
     "tdmix_loglik_components_noalloc": (_c_i, [_c_i, ctypes.c_int64, _c_p, _c_p, ctypes.c_int64, _c_p, _c_p, _c_p,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _c_p, _c_p]),
+    "tdmix_trace": (_c_i, [_c_p, _c_i]),
+    "tdmix_trace_read": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_last_error": (ctypes.c_char_p, [_c_p]),
     "tdmix_destroy": (None, [_c_p]),
 }
@@ -225,7 +227,7 @@ class TDMix:
         self._check(self._lib.tdmix_norm_matrix(self._ctx, out.ctypes.data))
         return (out[0::2] + 1j * out[1::2]).reshape(U, U)
 
-    PROF_CLASSES = ("prepare", "mc", "data", "final")
+    PROF_CLASSES = ("eval", "precompute")
 
     def profile(self, enable: bool = True):
         """Times every kernel launch of this context with CUDA events."""
@@ -233,10 +235,23 @@ class TDMix:
 
     def profile_read(self, reset: bool = True) -> dict:
         """{kernel class: (total ms, launches)} since the last reset."""
-        ms = np.zeros(4)
-        n = np.zeros(4, dtype=np.int64)
+        ms = np.zeros(len(self.PROF_CLASSES))
+        n = np.zeros(len(self.PROF_CLASSES), dtype=np.int64)
         self._check(self._lib.tdmix_profile_read(self._ctx, ms.ctypes.data, n.ctypes.data, int(reset)))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROF_CLASSES)}
+
+    TRACE_PHASES = ("start", "constants", "data_done", "mc_done", "partials", "reduced", "nll", "end")
+
+    def trace(self, enable: bool = True):
+        """Per-block phase timestamps of the evaluation kernel."""
+        self._check(self._lib.tdmix_trace(self._ctx, int(enable)))
+
+    def trace_read(self) -> np.ndarray:
+        """(blocks, phases) array of ns stamps of the last evaluation."""
+        buf = np.zeros(1024 * len(self.TRACE_PHASES), dtype=np.uint64)
+        nb = ctypes.c_int()
+        self._check(self._lib.tdmix_trace_read(self._ctx, buf.ctypes.data, ctypes.byref(nb)))
+        return buf[:nb.value * len(self.TRACE_PHASES)].reshape(nb.value, len(self.TRACE_PHASES))
 
     def close(self):
         if getattr(self, "_ctx", None):
