@@ -164,6 +164,52 @@ int tdmix_profile(tdmix_ctx* ctx, int enable);
  * totals afterwards. */
 int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, int reset);
 
+/* ---- Serving ------------------------------------------------------------
+ * Many minimisers fitting independent pseudo-experiments (the paper's
+ * sensitivity study, Sec. 4, fits toy samples with a fixed model and
+ * floating x, y) submit (sample, parameters) requests concurrently.  The
+ * server keeps the model's resonance masses and widths fixed, so the MC
+ * normalisation sums are computed once and every resident sample keeps its
+ * per-event component cache.  A scheduler thread evaluates whatever is
+ * pending as one batched kernel launch; requests that arrive meanwhile join
+ * the next batch.  Samples are admitted into device memory by footprint
+ * (2U component values + one decay time per event); when the budget binds,
+ * least recently used samples without pending requests are evicted, and a
+ * request whose sample cannot be admitted yet waits for memory to free up.
+ * A request's result does not depend on which other requests share its
+ * batch.  All functions are thread-safe. */
+typedef struct tdmix_server tdmix_server;
+
+/* hbm_budget_bytes: device memory allowed for resident samples;
+ * max_slots: requests per batch at most (1 .. 1024). */
+int tdmix_server_create(const char* model_json, int precision, size_t hbm_budget_bytes, int max_slots,
+                        tdmix_server** out);
+/* The shared phase-space MC sample (host or device memory, see
+ * tdmix_events); computes the normalisation sums of the fixed model. */
+int tdmix_server_add_mc(tdmix_server* s, const tdmix_events* mc);
+/* Registers a data sample (copied to host memory; admitted to the device on
+ * demand); *sample_id receives its id. */
+int tdmix_server_add_sample(tdmix_server* s, const tdmix_events* data, int* sample_id);
+/* Queues an NLL + gradient evaluation of sample_id at params (host,
+ * num_params doubles; masses and widths must equal the model's values,
+ * else TDMIX_ERR_ARG).  *ticket identifies the request. */
+int tdmix_server_submit(tdmix_server* s, int sample_id, const double* params, uint64_t* ticket);
+/* Waits up to timeout_s seconds for a request: *nll and, if grad is not
+ * NULL, the gradient (host, num_params doubles; masses and widths get 0).
+ * TDMIX_ERR_TIMEOUT if it is not done in time (the request stays valid and
+ * can be waited for again); the request's own status otherwise. */
+int tdmix_server_wait(tdmix_server* s, uint64_t ticket, double* nll, double* grad, double timeout_s);
+/* Latency percentiles (submit to completion, microseconds) and throughput
+ * (completed requests per second between the first submit and the last
+ * completion) since creation or the last reset. */
+int tdmix_server_stats(tdmix_server* s, double* p50_us, double* p99_us, double* evals_per_s);
+int tdmix_server_reset_stats(tdmix_server* s);
+/* Device memory currently held by resident samples. */
+int tdmix_server_resident_bytes(tdmix_server* s, size_t* bytes);
+const char* tdmix_server_last_error(const tdmix_server* s);
+/* Stops the scheduler (pending requests are dropped) and frees everything. */
+void tdmix_server_destroy(tdmix_server* s);
+
 /* Tracing (library extension for measurement; the paper has no
  * counterpart).  With tracing on, every block of the evaluation kernel
  * records TDMIX_TRACE_PHASES globaltimer stamps (ns): start, per-evaluation

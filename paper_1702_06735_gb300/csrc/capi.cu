@@ -413,6 +413,62 @@ int result_status(tdmix_ctx* ctx) {
 
 }  // namespace
 
+namespace tdmix {
+namespace internal {
+
+cudaStream_t stream_of(tdmix_ctx* ctx) { return ctx->stream; }
+int num_sms_of(tdmix_ctx* ctx) { return ctx->num_sms; }
+const CompiledModel& model_of(tdmix_ctx* ctx) { return ctx->model; }
+const ShapeOps* ops_of(tdmix_ctx* ctx) { return ctx->ops; }
+const DevModel* dev_model_of(tdmix_ctx* ctx) { return ctx->d_model; }
+const int* dev_floating_of(tdmix_ctx* ctx) { return ctx->d_floating; }
+bool is_f32(tdmix_ctx* ctx) { return ctx->f32; }
+double inv_sum_w_of(tdmix_ctx* ctx) { return ctx->inv_sum_w; }
+const double* gram_store_of(tdmix_ctx* ctx) { return ctx->d_gram; }
+std::string& error_of(tdmix_ctx* ctx) { return ctx->err; }
+
+// Computes the component cache of a data sample at host parameters `params`
+// (one full evaluation with the loaded MC) and hands its device buffers to
+// the caller: *cache ([2U][pitch] working precision), *t ([pitch] f64).
+int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* params, void** cache, double** t,
+                         int64_t* pitch, double* sum_t) {
+  int rc = load_sample(ctx, ev, true, ctx->data);
+  if (rc) return rc;
+  ctx->cache_valid = false;
+  if ((rc = enqueue_eval(ctx, params, true, false, nullptr))) return rc;
+  TDMIX_CK(cudaStreamSynchronize(ctx->stream));
+  Sample& d = ctx->data;
+  *cache = d.dev.cache;
+  *t = const_cast<double*>(d.dev.t);
+  *pitch = d.dev.pitch;
+  *sum_t = ctx->sum_t;
+  // keep cache and t alive, free the planes and scratch
+  std::vector<void*> keep;
+  for (void* p : d.owned)
+    if (p == d.dev.cache || p == d.dev.t) keep.push_back(p);
+    else cudaFree(p);
+  d.owned.clear();
+  d = Sample{};
+  ctx->cache_valid = false;
+  return TDMIX_OK;
+}
+
+// Runs one full evaluation at host `params` with a one-event stand-in data
+// sample, leaving the MC column totals (normalisation sums) in the context.
+int compute_mc_totals(tdmix_ctx* ctx, const double* params, const tdmix_events* one_event) {
+  int rc = load_sample(ctx, one_event, true, ctx->data);
+  if (rc) return rc;
+  ctx->cache_valid = false;
+  if ((rc = enqueue_eval(ctx, params, true, false, nullptr))) return rc;
+  TDMIX_CK(cudaStreamSynchronize(ctx->stream));
+  free_sample(ctx->data);
+  ctx->cache_valid = false;
+  return TDMIX_OK;
+}
+
+}  // namespace internal
+}  // namespace tdmix
+
 extern "C" {
 
 int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {

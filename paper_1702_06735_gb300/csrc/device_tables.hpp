@@ -62,6 +62,36 @@ constexpr int kTracePhases = 8;
 constexpr int kDataTileCostF32 = 4;
 constexpr int kDataTileCostF64 = 1;
 
+constexpr int kServeMaxChunks = 256;     // chunks per request at most
+constexpr int kServeMaxRequests = 1024;  // requests per batch at most
+
+// One request of a serving batch (see serve.cuh).
+struct ServeReq {
+  const void* cache;     // [2U][pitch] components (working precision)
+  const double* t;       // [pitch] decay times
+  int64_t n, pitch;
+  int32_t chunk_begin;   // first row of this request in the partial array
+  int32_t n_chunks;
+  int32_t chunk_tiles;   // tiles per chunk (the last chunk may have fewer)
+  int32_t n_tiles;
+  double sum_t;
+};
+
+struct ServeArgs {
+  const ServeReq* reqs;
+  int n_req;
+  int total_chunks;
+  const double* params;     // [n_req][n_params]
+  const DevModel* dm;
+  const int* floating;
+  const double* mc_cols;    // MC column totals of the fixed model
+  double inv_sum_w;
+  void* part;               // float2 [total_chunks][WD] chunk partials
+  unsigned* counters;       // [n_req] chunks finished (returned to 0)
+  double* results;          // [n_req][kResHeader + n_params]
+  int* err;
+};
+
 // Result vector written by the evaluation kernel: [nll, N, n_bad or status, sum ln B, grad...]
 constexpr int kResHeader = 4;
 

@@ -3,6 +3,7 @@
 #include <string>
 
 #include "fused.cuh"
+#include "serve.cuh"
 #include "kernels.hpp"
 #include "shapes_gen.h"
 
@@ -53,6 +54,23 @@ struct Ops {
     }
     return cudaErrorNotSupported;
   }
+  static cudaError_t serve(bool grad, int grid, cudaStream_t st, const ServeArgs& a) {
+    if constexpr (kOk) {
+      const int smem = ServeLayout<Prec, S>::smem_bytes();
+      static bool attr = false;
+      auto kern = grad ? k_serve<Prec, S, true> : k_serve<Prec, S, false>;
+      if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_serve<Prec, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(k_serve<Prec, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      kern<<<grid, kTile, smem, st>>>(a);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
+  }
 };
 
 }  // namespace
@@ -62,7 +80,7 @@ const ShapeOps* TDMIX_FIND(const std::string& sig) {
   if (Ops<shapes::S>::kOk && sig == shapes::S::sig()) {                                       \
     static const ShapeOps o = {shapes::S::sig(), shapes::S::U, shapes::S::NR,                 \
                                Layout<Prec, shapes::S>::WMC, Layout<Prec, shapes::S>::WD,     \
-                               &Ops<shapes::S>::eval};                                        \
+                               &Ops<shapes::S>::eval, &Ops<shapes::S>::serve};                \
     return &o;                                                                                \
   }
   TDMIX_FOR_EACH_SHAPE(TDMIX_SHAPE_ENTRY)

@@ -241,28 +241,29 @@ __device__ inline void kappa_derivatives(const DevModel* dm, int r, double m0, d
 // Work is spread over threads so that only short chains of double-precision
 // operations are dependent; the logarithm runs on one thread while the
 // others form the gradient.
+// Likelihood from the MC column totals `mcs` and the data column totals
+// `ds` of one sample: writes [nll, N, n_bad or status, sum ln B, grad...]
+// to `res`.  Used by the last block of an evaluation and, in serving, by the
+// last chunk of each request.  `err` is a bounded-wait failure flag (read
+// and cleared).
 template <class S>
-__device__ inline void final_epilogue(const EvalArgs& a, CtaConst& cc, const double* colsum, bool want_grad,
-                                      bool have_res_grad, unsigned long long* trace) {
+__device__ inline void finish_likelihood(double* res, int nc, int np, const CtaConst& cc, const double* mcs,
+                                         const double* ds, double Nd, double sum_t, double inv_sw, bool want_grad,
+                                         bool have_res_grad, int* err, unsigned long long* trace) {
   constexpr int U = S::U, NR = S::NR;
-  constexpr int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2, WMC = 1 + NRE + NIM + 2 * NR;
-  const double* mcs = colsum;
-  const double* ds = colsum + WMC;
+  constexpr int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2;
   __shared__ double prod[2][U][U][2];
   __shared__ double vv[2][U][2];  // S cA, S cB (unnormalised)
   __shared__ double sh[8];        // AA, BB, Xr, Xi (unnormalised), nbar, sc
   const int tid = threadIdx.x;
-  const int nc = a.dm->n_chains, np = a.dm->n_params;
-  double* res = a.result;
-  const int timed_out = *a.err;
+  const int timed_out = *err;
   const int status = timed_out ? -7 : (cc.nonfinite ? -5 : (cc.domain ? -6 : 0));
   if (status != 0) {
     __syncthreads();
-    if (tid == 0 && timed_out) *a.err = 0;
+    if (tid == 0 && timed_out) *err = 0;
     for (int k = tid; k < kResHeader + np; k += blockDim.x) res[k] = k == 2 ? double(status) : nan("");
     return;
   }
-  const double inv_sw = a.inv_sum_w;
   // products S_jk c_k, thread (which, j, k)
   for (int e = tid; e < 2 * U * U; e += blockDim.x) {
     const int which = e / (U * U), j = (e / U) % U, k = e % U;
@@ -302,7 +303,6 @@ __device__ inline void final_epilogue(const EvalArgs& a, CtaConst& cc, const dou
   }
   __syncthreads();
   const double al = cc.alpha, be = cc.beta, gc = cc.gc, dc = cc.dc, x = cc.x, y = cc.y, gamma = cc.gamma;
-  const double Nd = double(a.data.n);
   const double AA = sh[0], BB = sh[1], Xr = sh[2], Xi = sh[3];
   const double nbar = (al * AA + be * BB - 2.0 * gc * Xr - 2.0 * dc * Xi) * inv_sw;
   if (want_grad && tid == 32) sh[5] = Nd / nbar;  // d(N_d ln N) = N_d dnbar / nbar
@@ -310,13 +310,13 @@ __device__ inline void final_epilogue(const EvalArgs& a, CtaConst& cc, const dou
   if (tid == 0) {
     const double N = nbar / gamma;
     const double sum_lnb = ds[0], nbad = ds[1];
-    double nll = -sum_lnb + gamma * a.sum_t + Nd * log(N);
+    double nll = -sum_lnb + gamma * sum_t + Nd * log(N);
     if (nbad > 0 || !(N > 0)) nll = nan("");
     res[0] = nll;
     res[1] = N;
     res[2] = nbad;
     res[3] = sum_lnb;
-    if (timed_out) *a.err = 0;
+    if (timed_out) *err = 0;
     if (trace) trace[6] = global_ns();
   }
   if (!want_grad) return;
@@ -371,6 +371,14 @@ __device__ inline void final_epilogue(const EvalArgs& a, CtaConst& cc, const dou
     res[kResHeader + k] = cc.floating[k] ? -ds[2] + sc * dn_dx : 0.0;
     res[kResHeader + k + 1] = cc.floating[k + 1] ? -ds[3] + sc * dn_dy : 0.0;
   }
+}
+
+template <class S>
+__device__ inline void final_epilogue(const EvalArgs& a, CtaConst& cc, const double* colsum, bool want_grad,
+                                      bool have_res_grad, unsigned long long* trace) {
+  constexpr int WMC = Layout<PrecF64, S>::WMC;
+  finish_likelihood<S>(a.result, a.dm->n_chains, a.dm->n_params, cc, colsum, colsum + WMC, double(a.data.n),
+                       a.sum_t, a.inv_sum_w, want_grad, have_res_grad, a.err, trace);
 }
 
 template <class P, class S, bool FULL, bool GRAD, bool WEIGHTED>

@@ -27,6 +27,8 @@ struct ShapeOps {
   // full: recompute components and run the MC tiles; otherwise read the
   // component cache and reuse the stored MC totals.
   cudaError_t (*eval)(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a, const int* floating);
+  // batched evaluation of serving requests (see serve.cuh)
+  cudaError_t (*serve)(bool grad, int grid, cudaStream_t st, const ServeArgs& a);
 };
 
 // Specialisation compiled for a model signature, or null.

@@ -1,0 +1,237 @@
+// Batched evaluation of many likelihood requests (serving).
+//
+// A request is (sample, parameter vector) with the amplitude model's masses
+// and widths fixed, so each resident sample keeps its per-event component
+// cache and the MC normalisation sums are shared by all requests.  One
+// persistent kernel evaluates a whole batch: the work items are chunks of
+// consecutive event tiles of one request; a block takes chunks b, b + grid,
+// ...  Each chunk's partial sums go to its own row, and the block that
+// finishes the last chunk of a request sums that request's rows in chunk
+// order and forms its NLL and gradient.  The chunk partition of a request
+// depends only on its size, so a request's result does not depend on which
+// other requests share the batch.
+#pragma once
+#include "fused.cuh"
+
+namespace tdmix {
+
+
+template <class P, class S>
+struct ServeLayout {
+  using T = typename P::T;
+  static constexpr int U = S::U, NR = S::NR;
+  static constexpr int WD = 4 + 4 * U + 2 * NR;
+  static constexpr int stage_bytes = 2 * U * kTile * int(sizeof(T)) + kTile * 8;
+  static constexpr int smem_bytes() {
+    const int st = 2 * stage_bytes, pr = kServeMaxChunks * WD * 8;
+    return st > pr ? st : pr;
+  }
+};
+
+template <class P, class S, bool GRAD>
+__global__ void __launch_bounds__(kTile, 1) k_serve(ServeArgs a) {
+  using T = typename P::T;
+  using LY = ServeLayout<P, S>;
+  constexpr int U = S::U, NR = S::NR, WD = LY::WD, TE = kTile, ES = int(sizeof(T));
+  constexpr int WMC = Layout<P, S>::WMC;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[3];
+  __shared__ CtaConst cc;
+  __shared__ BlockConst<T> bc;
+  __shared__ double red[kTile / 32][WD];
+  __shared__ double colsum[WMC + WD];
+  __shared__ int chunk_start[kServeMaxRequests + 1];
+  __shared__ unsigned is_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = gridDim.x;
+  unsigned char* stage[2] = {smem_raw, smem_raw + LY::stage_bytes};
+  for (int r = tid; r < a.n_req; r += blockDim.x) chunk_start[r] = a.reqs[r].chunk_begin;
+  if (tid == 0) {
+    chunk_start[a.n_req] = a.total_chunks;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int np = a.dm->n_params, nc = a.dm->n_chains;
+  uint32_t uses = 0;  // completed barrier phases (both stages), for parity tracking
+  bool failed = false;
+
+  for (int c = blockIdx.x; c < a.total_chunks && !failed; c += G) {
+    int lo = 0, hi = a.n_req;  // request r with chunk_start[r] <= c < chunk_start[r + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (chunk_start[mid] <= c) lo = mid;
+      else hi = mid;
+    }
+    const int r = lo;
+    const ServeReq q = a.reqs[r];
+    const int lc = c - q.chunk_begin;
+    const int t0 = lc * q.chunk_tiles;
+    const int t1 = min(t0 + q.chunk_tiles, q.n_tiles);
+    const int ntl = t1 - t0;
+    auto issue = [&](int j, uint32_t use) {  // tile t0 + j into stage use & 1
+      const int st = int(use & 1);
+      const int64_t off = int64_t(t0 + j) * TE;
+      mbar_arrive_expect_tx(&bars[st], uint32_t(2 * U * TE * ES + TE * 8));
+      T* dst = reinterpret_cast<T*>(stage[st]);
+      for (int p = 0; p < 2 * U; ++p)
+        bulk_g2s(dst + p * TE, static_cast<const T*>(q.cache) + p * q.pitch + off, TE * ES, &bars[st]);
+      bulk_g2s(stage[st] + 2 * U * TE * ES, q.t + off, TE * 8, &bars[st]);
+    };
+    if (tid == 0) {
+      issue(0, uses);
+      if (ntl > 1) issue(1, uses + 1);
+    }
+    derive_constants<T>(a.params + size_t(r) * np, a.dm, a.floating, cc, bc);
+    __syncthreads();
+
+    double lnb = 0.0;
+    int bad = 0;
+    T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
+    for (int j = 0; j < ntl; ++j, ++uses) {
+      const int st = int(uses & 1);
+      const bool ok = mbar_wait_bounded(&bars[st], (uses >> 1) & 1u, kWaitNs);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      const int64_t i = int64_t(t0 + j) * TE + tid;
+      if (i < q.n) {
+        const T* sbase = reinterpret_cast<const T*>(stage[st]);
+        const double t_e = reinterpret_cast<const double*>(stage[st] + 2 * U * TE * ES)[tid];
+        EventCore<P, S> ev;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          ev.ar[k] = sbase[k * TE + tid];
+          ev.ai[k] = sbase[(U + k) * TE + tid];
+        }
+        T Ar_, Ai_, Br_, Bi_;
+        ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
+        const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
+        const double gt = bc.gamma * t_e;
+        double cha, sha, cb, sb;
+        mixing_trig(0.5 * bc.y * gt, 0.5 * bc.x * gt, cha, sha, cb, sb);
+        const double chr = cha * cb, chi = sha * sb, shr = sha * cb, shi = cha * sb;
+        const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);
+        const double Zi = chr * Ai + chi * Ar - (shr * Bi + shi * Br);
+        const double B = 2.0 * (Zr * Zr + Zi * Zi);
+        if (B > 0.0 && B < INFINITY) {
+          lnb += log(B);
+          if constexpr (GRAD) {
+            T cr, ci, sr, si, Zrt, Zit;
+            if constexpr (P::kF32) {
+              const float gtf = float(bc.gamma) * float(t_e);
+              float chf, shf, cbf, sbf;
+              mixing_trig_f32(0.5f * float(bc.y) * gtf, 0.5f * float(bc.x) * gtf, chf, shf, cbf, sbf);
+              cr = chf * cbf; ci = shf * sbf; sr = shf * cbf; si = chf * sbf;
+              Zrt = 0; Zit = 0;
+              cmac(Zrt, Zit, cr, ci, Ar_, Ai_);
+              cmac(Zrt, Zit, -sr, -si, Br_, Bi_);
+            } else {
+              cr = chr; ci = chi; sr = shr; si = shi;
+              Zrt = Zr; Zit = Zi;
+            }
+            const T iz = rcp<T>(fma(Zrt, Zrt, Zit * Zit));
+            const T Vr = Zrt * iz, Vi = -Zit * iz;
+            const T tAr = fma(Vr, cr, -Vi * ci), tAi = fma(Vr, ci, Vi * cr);
+            const T tBr = -fma(Vr, sr, -Vi * si), tBi = -fma(Vr, si, Vi * sr);
+            T Dr = 0, Di = 0;
+            cmac(Dr, Di, sr, si, Ar_, Ai_);
+            cmac(Dr, Di, -cr, -ci, Br_, Bi_);
+            const T tg = P::kF32 ? T(float(bc.gamma) * float(t_e)) : T(gt);
+            gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
+            gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+              cmac(gAr[k], gAi[k], tAr, tAi, ev.ar[k], ev.ai[k]);
+              cmac(gBr[k], gBi[k], tBr, tBi, ev.ar[k], ev.ai[k]);
+            }
+          }
+        } else {
+          bad += 1;
+        }
+      }
+      __syncthreads();
+      if (tid == 0 && j + 2 < ntl) issue(j + 2, uses + 2);
+    }
+    if (failed) {
+      if (tid == 0) {
+        atomicOr(a.err, 1);
+        for (uint32_t u = uses; u < uses + 2; ++u) mbar_wait_bounded(&bars[u & 1], (u >> 1) & 1u, kWaitNs);
+      }
+      __syncthreads();
+    }
+    // chunk partial -> its row
+    {
+      const double v0 = warp_sum(lnb), v1 = warp_sum(double(bad));
+      if (lane == 0) {
+        red[warp][0] = v0;
+        red[warp][1] = v1;
+      }
+      T vt[2 + 4 * U];
+      vt[0] = gx;
+      vt[1] = gy;
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        vt[2 + k] = gAr[k];
+        vt[2 + U + k] = gAi[k];
+        vt[2 + 2 * U + k] = gBr[k];
+        vt[2 + 3 * U + k] = gBi[k];
+      }
+#pragma unroll
+      for (int v = 0; v < 2 + 4 * U; ++v) {
+        const T s = warp_sum(vt[v]);
+        if (lane == 0) red[warp][2 + v] = double(s);
+      }
+    }
+    __syncthreads();
+    float2* part = static_cast<float2*>(a.part);
+    for (int v = tid; v < WD; v += blockDim.x) {
+      double s = 0;
+      for (int w = 0; w < kTile / 32; ++w) s += red[w][v];
+      part[size_t(c) * WD + v] = v < 4 + 4 * U ? to_df(s) : make_float2(0.f, 0.f);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(a.counters + r, 1u) == unsigned(q.n_chunks - 1);
+    __syncthreads();
+    if (!is_last) continue;
+    // ---- last chunk of request r: sum its rows in chunk order, then the likelihood
+    __threadfence();
+    float2* sp = reinterpret_cast<float2*>(smem_raw);
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      mbar_init(&bars[2], 1);
+      mbar_fence_init();
+      const uint32_t bytes = uint32_t(q.n_chunks) * uint32_t(WD) * 8u;
+      mbar_arrive_expect_tx(&bars[2], bytes);
+      bulk_g2s(sp, part + size_t(q.chunk_begin) * WD, bytes, &bars[2]);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bars[2], 0, kWaitNs);
+    if (__syncthreads_or(!ok) && tid == 0) atomicOr(a.err, 1);
+    for (int v = tid; v < WMC; v += blockDim.x) colsum[v] = a.mc_cols[v];
+    for (int v = tid; v < WD; v += blockDim.x) {
+      float s = 0.f, e = 0.f;
+      for (int row = 0; row < q.n_chunks; ++row) {
+        const float2 x = sp[size_t(row) * WD + v];
+        float t, er;
+        two_sum(s, x.x, t, er);
+        s = t;
+        e += er + x.y;
+      }
+      colsum[WMC + v] = double(s) + double(e);
+    }
+    __syncthreads();
+    if (tid == 0) a.counters[r] = 0u;
+    finish_likelihood<S>(a.results + size_t(r) * (kResHeader + np), nc, np, cc, colsum, colsum + WMC,
+                         double(q.n), q.sum_t, a.inv_sum_w, GRAD, false, a.err, nullptr);
+    __syncthreads();
+    // the bulk-copy target overlapped the stages: stages restart clean below
+  }
+}
+
+}  // namespace tdmix

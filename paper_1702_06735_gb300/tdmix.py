@@ -41,6 +41,16 @@ _SIGNATURES = {
     "tdmix_profile_read": (_c_i, [_c_p, _c_p, _c_p, _c_i]),
     "tdmix_loglik_components_noalloc": (_c_i, [_c_i, ctypes.c_int64, _c_p, _c_p, ctypes.c_int64, _c_p, _c_p, _c_p,
                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _c_p, _c_p]),
+    "tdmix_server_create": (_c_i, [ctypes.c_char_p, _c_i, ctypes.c_size_t, _c_i, ctypes.POINTER(_c_p)]),
+    "tdmix_server_add_mc": (_c_i, [_c_p, _c_p]),
+    "tdmix_server_add_sample": (_c_i, [_c_p, _c_p, ctypes.POINTER(_c_i)]),
+    "tdmix_server_submit": (_c_i, [_c_p, _c_i, _c_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "tdmix_server_wait": (_c_i, [_c_p, ctypes.c_uint64, _c_p, _c_p, ctypes.c_double]),
+    "tdmix_server_stats": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
+    "tdmix_server_reset_stats": (_c_i, [_c_p]),
+    "tdmix_server_resident_bytes": (_c_i, [_c_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "tdmix_server_last_error": (ctypes.c_char_p, [_c_p]),
+    "tdmix_server_destroy": (None, [_c_p]),
     "tdmix_trace": (_c_i, [_c_p, _c_i]),
     "tdmix_trace_read": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_last_error": (ctypes.c_char_p, [_c_p]),
@@ -257,6 +267,77 @@ class TDMix:
         if getattr(self, "_ctx", None):
             self._lib.tdmix_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TDMixServer:
+    """Batched, continuously admitted NLL + gradient requests (tdmix_server)."""
+
+    def __init__(self, model, precision: str = "fp32", hbm_budget_bytes: int = 4 << 30, max_slots: int = 256):
+        self._lib = load_library()
+        self._s = ctypes.c_void_p()
+        prec = {"fp64": FP64, "fp32": FP32}[precision]
+        rc = self._lib.tdmix_server_create(model_json(model).encode(), prec, hbm_budget_bytes, max_slots,
+                                           ctypes.byref(self._s))
+        if rc != 0:
+            msg = self._lib.tdmix_server_last_error(self._s).decode() if self._s else ""
+            self.close()
+            raise TDMixError(rc, msg)
+        m = json.loads(model_json(model))
+        self.n_params = 2 * len(m["chains"]) + 2 * len(m["resonances"]) + 2
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TDMixError(rc, self._lib.tdmix_server_last_error(self._s).decode())
+
+    def add_mc(self, mc_p4, mc_w=None):
+        ev, keep = _planes(mc_p4, w=mc_w)
+        self._check(self._lib.tdmix_server_add_mc(self._s, ctypes.byref(ev)))
+
+    def add_sample(self, p4, t) -> int:
+        ev, keep = _planes(p4, t=t)
+        sid = ctypes.c_int()
+        self._check(self._lib.tdmix_server_add_sample(self._s, ctypes.byref(ev), ctypes.byref(sid)))
+        return sid.value
+
+    def submit(self, sample_id: int, params) -> int:
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        tk = ctypes.c_uint64()
+        self._check(self._lib.tdmix_server_submit(self._s, sample_id, p.ctypes.data, ctypes.byref(tk)))
+        return tk.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        """(nll, gradient) of a submitted request."""
+        v = np.empty(1)
+        g = np.empty(self.n_params)
+        self._check(self._lib.tdmix_server_wait(self._s, ticket, v.ctypes.data, g.ctypes.data, timeout_s))
+        return float(v[0]), g
+
+    def evaluate(self, sample_id: int, params, timeout_s: float = 60.0):
+        return self.wait(self.submit(sample_id, params), timeout_s)
+
+    def stats(self) -> dict:
+        a, b, c = np.empty(1), np.empty(1), np.empty(1)
+        self._check(self._lib.tdmix_server_stats(self._s, a.ctypes.data, b.ctypes.data, c.ctypes.data))
+        return {"p50_us": float(a[0]), "p99_us": float(b[0]), "evals_per_s": float(c[0])}
+
+    def reset_stats(self):
+        self._check(self._lib.tdmix_server_reset_stats(self._s))
+
+    def resident_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        self._check(self._lib.tdmix_server_resident_bytes(self._s, ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if getattr(self, "_s", None):
+            self._lib.tdmix_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:
