@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdmix", choices=["tdmix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--toys", type=int, default=32, help="pseudo-experiments in the serving toy study (0: skip)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: flat-phase-space data instead of accept/reject (same sizes, same kernels)")
     return ap.parse_args()
@@ -221,6 +222,72 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# serving toy study (fixed model, x and y floating, one minimiser per toy)
+# ----------------------------------------------------------------------------
+def run_toy_study(precision, pool_p4, pool_t, mc, n_toys, budget_fraction=0.4, clients=16):
+    """Pseudo-experiments with sizes log-uniform in [5,000, 500,000] (seeded),
+    drawn with replacement from the generated event pool, sharing one MC
+    sample; each is fitted (x, y floating) by its own BFGS minimiser that
+    submits NLL + gradient requests to the serving loop."""
+    import concurrent.futures as cf
+    from paper_1702_06735_gb300 import minimize
+    from paper_1702_06735_gb300.tdmix import TDMixError, TDMixServer
+
+    g = np.random.default_rng(5150)
+    sizes = np.exp(g.uniform(np.log(5_000), np.log(500_000), n_toys)).astype(int)
+    # device footprint of the toys' component caches (8 components, re + im,
+    # plus one f64 decay time per event); the budget is set below it so that
+    # admission binds and samples are evicted and re-admitted
+    per_event = 2 * 8 * (4 if precision == "fp32" else 8) + 8
+    budget_bytes = int(budget_fraction * sum(((n + 255) // 256) * 256 for n in sizes) * per_event)
+    srv = TDMixServer(MODEL, precision, hbm_budget_bytes=budget_bytes, max_slots=256)
+    srv.add_mc(mc)
+    ids = []
+    for n in sizes:
+        idx = g.integers(0, len(pool_t), n)
+        ids.append(srv.add_sample(pool_p4[idx], pool_t[idx]))
+    from paper_1702_06735_gb300.tdmix import TDMix
+    tmp = TDMix(MODEL, precision)
+    start = tmp.default_params()
+    tmp.close()
+    mask = np.zeros(len(start), dtype=bool)
+    mask[-2:] = True
+    scale = np.ones(len(start))
+    scale[-2:] = 1e-3
+    n_evals = [0] * n_toys
+    fits = [None] * n_toys
+
+    def fit(k):
+        def fg(p):
+            n_evals[k] += 1
+            try:
+                return srv.evaluate(ids[k], p, timeout_s=600.0)
+            except TDMixError as e:
+                if e.code in (-5, -6):
+                    return float("inf"), np.full(len(p), np.nan)
+                raise
+        x0 = start.copy()
+        x0[-2] += 0.001 * (k % 3 - 1)
+        x0[-1] -= 0.001 * (k % 2)
+        r = minimize.bfgs(fg, x0, floating=mask, scale=scale, gtol=1e-3, edm_tol=1e-6, max_iter=60)
+        fits[k] = (r.x[-2], r.x[-1], r.converged)
+
+    srv.reset_stats()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=clients) as ex:
+        list(ex.map(fit, range(n_toys)))
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    out = {"toys": n_toys, "events_total": int(sizes.sum()), "min_events": int(sizes.min()),
+           "max_events": int(sizes.max()), "clients": clients, "evals": int(sum(n_evals)),
+           "p50_us": st["p50_us"], "p99_us": st["p99_us"], "evals_per_s": st["evals_per_s"], "wall_s": wall,
+           "hbm_budget_bytes": budget_bytes, "converged": int(sum(1 for f in fits if f and f[2])),
+           "mc_events": int(len(mc))}
+    srv.close()
+    return out
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def run_tdmix(args):
@@ -376,6 +443,10 @@ def run_tdmix(args):
         "generation": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in gen_stats.items()},
         "wall_s_timed_region": wall32,
     }
+    if args.toys > 0:
+        from paper_1702_06735_gb300 import samples as smp
+        mc2 = smp.flat_phase_space(2_000_000, smp.rng(WORKLOAD_ID, 40 + rank))
+        out["toy_study"] = {prec: run_toy_study(prec, data, t, mc2, args.toys) for prec in ("fp32", "fp64")}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = time_oracle(data, t, mc, CPU_SAMPLE, evals=5, warmup=1)
     print(json.dumps(out), flush=True)
