@@ -130,7 +130,11 @@ int tdmix_load_events(tdmix_ctx* ctx, const tdmix_events* data, const tdmix_even
  * reuses the per-event component cache and the stored MC normalisation
  * matrix; otherwise every step is recomputed.  Host outputs: returns
  * TDMIX_ERR_NONFINITE / TDMIX_ERR_DOMAIN for invalid parameters or a rate
- * <= 0.  Device outputs: such failures are reported as NaN values. */
+ * <= 0.  Device outputs: such failures are reported as NaN values.
+ * One kernel launch does the whole evaluation: host params travel in its
+ * arguments, device params are read by it when the stream reaches it; it
+ * writes device outputs itself and host outputs through mapped pinned
+ * memory, so no separate copy is enqueued. */
 int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* grad_out);
 
 /* Per-event rate e^{-Gamma t} B(e) of Eq. (mix) for every data event

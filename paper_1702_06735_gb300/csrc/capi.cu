@@ -27,8 +27,6 @@ using namespace tdmix;
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int64_t kPitchAlign = 256;
 
 struct Sample {
   SampleDev dev{};
@@ -45,18 +43,16 @@ struct tdmix_ctx {
   const ShapeOps* ops = nullptr;
   cudaStream_t stream = nullptr;
   int device = 0, num_sms = 0;
-  DevModel* d_model = nullptr;
-  double* d_params = nullptr;
+  DevModel* d_model = nullptr;  // structure tables of the kinematic precompute
+  ModelConst km{};               // model constants passed to the likelihood kernels by value
   double* d_result = nullptr;
   double* d_gram = nullptr;
   double* d_sumt = nullptr;
-  int* d_floating = nullptr;
-  int* d_err = nullptr;  // timeout flag of bounded device waits
   unsigned long long* d_trace = nullptr;  // per-block phase stamps of the last evaluation (tracing on)
   int64_t* d_ranges = nullptr;            // per-block MC tile ranges [num_sms + 1]
   int64_t ranges_key[3] = {-1, -1, -1};   // (data tiles, MC tiles, grid) the ranges were made for
-  double* h_params = nullptr;  // pinned
-  double* h_result = nullptr;  // pinned
+  double* h_result = nullptr;      // pinned, mapped: written by the kernel for host callers
+  double* d_result_map = nullptr;  // device address of h_result
   void* d_part = nullptr;         // block partials of the evaluation kernel (float2 [width][num_sms])
   unsigned* d_counter = nullptr;  // blocks finished (returned to 0 by the kernel)
   Sample data, mc;
@@ -148,6 +144,28 @@ DevModel make_dev_model(const CompiledModel& m) {
   return d;
 }
 
+ModelConst make_model_const(const CompiledModel& m, const std::vector<int>& floating) {
+  ModelConst k;
+  std::memset(&k, 0, sizeof k);
+  k.n_chains = int(m.chains.size());
+  k.n_params = m.n_params();
+  k.r_res = m.r_res;
+  k.gamma = 1.0 / m.tau;
+  k.tau = m.tau;
+  for (size_t r = 0; r < m.res.size(); ++r) {
+    k.res_ma[r] = m.res[r].ma;
+    k.res_mb[r] = m.res[r].mb;
+    k.res_shape[r] = int8_t(m.res[r].shape);
+    k.res_L[r] = int8_t(m.res[r].L);
+  }
+  for (size_t c = 0; c < m.chains.size(); ++c) {
+    k.chain_comp[c] = int8_t(m.chain_comp[c]);
+    k.chain_amp[c] = int8_t(m.chains[c].amp);
+  }
+  for (int q = 0; q < m.n_params(); ++q) k.floating[q] = floating[q] ? 1 : 0;
+  return k;
+}
+
 // Host-side screening of a parameter vector (host pointer only).
 int check_params(tdmix_ctx* ctx, const double* p) {
   const CompiledModel& m = ctx->model;
@@ -193,17 +211,18 @@ int prof_mark(tdmix_ctx* ctx, int c, int phase) {
   return TDMIX_OK;
 }
 
+// Copies one event sample to the device and runs the kinematic precompute
+// into its tile-major planes (see SampleDev).
 int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s) {
-  const CompiledModel& m = ctx->model;
   if (ev->n < 1) return fail(ctx, TDMIX_ERR_ARG, "an event sample needs n >= 1");
   for (int a = 0; a < 4; ++a)
     for (int c = 0; c < 4; ++c)
       if (!ev->p[a][c]) return fail(ctx, TDMIX_ERR_ARG, "missing momentum plane");
   if (is_data && !ev->t) return fail(ctx, TDMIX_ERR_ARG, "the data sample needs decay times");
   free_sample(s);
+  const ShapeOps* ops = ctx->ops;
   const int64_t n = ev->n;
-  const int64_t pitch = (n + kPitchAlign - 1) / kPitchAlign * kPitchAlign;
-  const size_t es = ctx->f32 ? sizeof(float) : sizeof(double);
+  const int64_t n_tiles = (n + kTileEvents - 1) / kTileEvents;
   cudaStream_t st = ctx->stream;
   int rc;
   Momenta mom;
@@ -211,6 +230,25 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);
     for (void* p : temps) cudaFree(p);
+  };
+  auto fail_clean = [&](int code, const std::string& msg) {
+    cleanup();
+    free_sample(s);
+    return fail(ctx, code, msg);
+  };
+  // f64 device copy of a per-event host array (or the caller's device array)
+  auto on_device = [&](const double* src, const double** out) -> int {
+    if (ev->on_device) {
+      *out = src;
+      return TDMIX_OK;
+    }
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, size_t(n) * sizeof(double)) != cudaSuccess) return TDMIX_ERR_NOMEM;
+    temps.push_back(buf);
+    if (cudaMemcpyAsync(buf, src, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return TDMIX_ERR_CUDA;
+    *out = static_cast<const double*>(buf);
+    return TDMIX_OK;
   };
   if (ev->on_device) {
     for (int a = 0; a < 4; ++a)
@@ -224,83 +262,36 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
       for (int c = 0; c < 4; ++c) {
         double* dst = static_cast<double*>(buf) + size_t(a * 4 + c) * n;
         e = cudaMemcpyAsync(dst, ev->p[a][c], n * sizeof(double), cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) {
-          cleanup();
-          return fail(ctx, TDMIX_ERR_CUDA, std::string("momentum copy: ") + cudaGetErrorString(e));
-        }
+        if (e != cudaSuccess) return fail_clean(TDMIX_ERR_CUDA, std::string("momentum copy: ") + cudaGetErrorString(e));
         mom.p[a][c] = dst;
       }
   }
+  const double* t_dev = nullptr;
+  const double* w_dev = nullptr;
+  if (is_data && (rc = on_device(ev->t, &t_dev))) return fail_clean(rc, "decay time staging");
+  if (!is_data && ev->w && (rc = on_device(ev->w, &w_dev))) return fail_clean(rc, "weight staging");
+
   SampleDev& d = s.dev;
   d.n = n;
-  d.pitch = pitch;
-  const int NT = m.U * m.NO;
-  if ((rc = dalloc(ctx, s, &d.s, size_t(ctx->f32 ? 2 : 1) * m.NS() * pitch * es)) ||
-      (rc = dalloc(ctx, s, &d.x, size_t(m.NX()) * pitch * es)) ||
-      (rc = dalloc(ctx, s, &d.k, size_t(NT) * pitch * es))) {
-    cleanup();
-    free_sample(s);
-    return rc;
-  }
+  d.n_tiles = n_tiles;
+  d.weighted = w_dev ? 1 : 0;
+  d.tile_bytes = is_data ? ops->data_tile_bytes : (w_dev ? ops->mc_tile_bytes_weighted : ops->mc_tile_bytes);
+  void* planes = nullptr;
+  if ((rc = dalloc(ctx, s, &planes, size_t(n_tiles) * d.tile_bytes))) return fail_clean(rc, ctx->err);
+  d.planes = planes;
+  cudaMemsetAsync(planes, 0, size_t(n_tiles) * d.tile_bytes, st);  // slots beyond n stay zero
   if (is_data) {
-    void* t = nullptr;
-    if ((rc = dalloc(ctx, s, &t, size_t(pitch) * sizeof(double))) ||
-        (rc = dalloc(ctx, s, &d.cache, size_t(2) * m.U * pitch * es)) ||
-        (rc = dalloc(ctx, s, reinterpret_cast<void**>(&s.rates), size_t(pitch) * sizeof(double)))) {
-      cleanup();
-      free_sample(s);
-      return rc;
-    }
-    cudaError_t e = cudaMemcpyAsync(t, ev->t, n * sizeof(double),
-                                    ev->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-      cleanup();
-      free_sample(s);
-      return fail(ctx, TDMIX_ERR_CUDA, std::string("time copy: ") + cudaGetErrorString(e));
-    }
-    d.t = static_cast<const double*>(t);
-  } else if (ev->w) {
-    void* w = nullptr;
-    if ((rc = dalloc(ctx, s, &w, size_t(pitch) * es))) {
-      cleanup();
-      free_sample(s);
-      return rc;
-    }
-    const double* wsrc = ev->w;
-    if (!ev->on_device) {
-      void* tmp = nullptr;
-      if (cudaMalloc(&tmp, n * sizeof(double)) != cudaSuccess) {
-        cleanup();
-        free_sample(s);
-        return fail(ctx, TDMIX_ERR_NOMEM, "weight staging buffer");
-      }
-      temps.push_back(tmp);
-      cudaMemcpyAsync(tmp, ev->w, n * sizeof(double), cudaMemcpyHostToDevice, st);
-      wsrc = static_cast<const double*>(tmp);
-    }
-    if (ctx->f32) launch_to_f32(wsrc, static_cast<float*>(w), n, st);
-    else cudaMemcpyAsync(w, wsrc, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    d.w = w;
-    double sw = 0;
-    launch_sum(wsrc, n, ctx->d_sumt, st);
-    cudaMemcpyAsync(&sw, ctx->d_sumt, sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess || !(sw > 0)) {
-      cleanup();
-      free_sample(s);
-      return fail(ctx, TDMIX_ERR_ARG, "MC weights must have a positive sum");
-    }
-    ctx->inv_sum_w = 1.0 / sw;
-  } else if (!is_data) {
-    ctx->inv_sum_w = 1.0 / double(n);
+    d.cache_tile_bytes = ops->cache_tile_bytes;
+    if ((rc = dalloc(ctx, s, &d.cache, size_t(n_tiles) * d.cache_tile_bytes)) ||
+        (rc = dalloc(ctx, s, reinterpret_cast<void**>(&s.rates), size_t(n) * sizeof(double))))
+      return fail_clean(rc, ctx->err);
+    cudaMemsetAsync(d.cache, 0, size_t(n_tiles) * d.cache_tile_bytes, st);
   }
   int prc = prof_mark(ctx, TDMIX_PROF_PRECOMPUTE, 0);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    cleanup();
-    free_sample(s);
-    return fail(ctx, TDMIX_ERR_CUDA, std::string("before precompute: ") + cudaGetErrorString(e));
-  }
-  launch_precompute(ctx->f32, mom, n, pitch, ctx->d_model, d.s, d.x, d.k, st);
+  if (e != cudaSuccess) return fail_clean(TDMIX_ERR_CUDA, std::string("before precompute: ") + cudaGetErrorString(e));
+  launch_precompute(ctx->f32, mom, n, ctx->d_model, planes, d.tile_bytes, ops->n_planes, t_dev, w_dev, d.cache,
+                    d.cache_tile_bytes, st);
   e = cudaGetLastError();
   if (!prc) prc = prof_mark(ctx, TDMIX_PROF_PRECOMPUTE, 1);
   if (prc) {
@@ -308,9 +299,10 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
     free_sample(s);
     return prc;
   }
-  if (e == cudaSuccess && is_data) {
-    launch_sum(d.t, n, ctx->d_sumt, st);
-    e = cudaMemcpyAsync(&ctx->sum_t, ctx->d_sumt, sizeof(double), cudaMemcpyDeviceToHost, st);
+  double sum = 0;
+  if (e == cudaSuccess && (t_dev || w_dev)) {
+    launch_sum(t_dev ? t_dev : w_dev, n, ctx->d_sumt, st);
+    e = cudaMemcpyAsync(&sum, ctx->d_sumt, sizeof(double), cudaMemcpyDeviceToHost, st);
   }
   cleanup();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -318,12 +310,27 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
     free_sample(s);
     return fail(ctx, TDMIX_ERR_CUDA, std::string("precompute: ") + cudaGetErrorString(e));
   }
+  if (is_data) {
+    ctx->sum_t = sum;
+  } else if (w_dev) {
+    if (!(sum > 0)) {
+      free_sample(s);
+      return fail(ctx, TDMIX_ERR_ARG, "MC weights must have a positive sum");
+    }
+    ctx->inv_sum_w = 1.0 / sum;
+  } else {
+    ctx->inv_sum_w = 1.0 / double(n);
+  }
   s.loaded = true;
   return TDMIX_OK;
 }
 
 // One evaluation: enqueue everything, leave the result in ctx->d_result.
-int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool want_grad, double* rates) {
+// `result` receives [nll, N, n_bad or status, sum ln B, grad...] (device
+// or mapped host memory); out_nll / out_grad are optional second
+// destinations (device memory).
+int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool want_grad, double* rates,
+                 double* result, double* out_nll = nullptr, double* out_grad = nullptr) {
   const CompiledModel& m = ctx->model;
   const int np = m.n_params(), nc = int(m.chains.size());
   cudaStream_t st = ctx->stream;
@@ -335,34 +342,33 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
     for (int k = 0; k < 2 * m.NR(); ++k)
       if (params[2 * nc + k] != ctx->last_res[k]) full = true;
   }
-  if (host_params) {
-    std::memcpy(ctx->h_params, params, np * sizeof(double));
-    TDMIX_CK(cudaMemcpyAsync(ctx->d_params, ctx->h_params, np * sizeof(double), cudaMemcpyHostToDevice, st));
-  } else {
-    TDMIX_CK(cudaMemcpyAsync(ctx->d_params, params, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  }
   int rc;
-  const int64_t items = (ctx->data.dev.n + 255) / 256 + (full ? (ctx->mc.dev.n + 255) / 256 : 0);
+  const int64_t items = ctx->data.dev.n_tiles + (full ? ctx->mc.dev.n_tiles : 0);
   const int grid = int(items < ctx->num_sms ? items : ctx->num_sms);
-  EvalArgs a{};
+  // parameters travel in the kernel arguments (host callers) or are read
+  // from the caller's device array
+  EvalArgs a;
+  std::memset(&a, 0, sizeof a);
   a.data = ctx->data.dev;
   a.mc = ctx->mc.dev;
-  a.params = ctx->d_params;
-  a.dm = ctx->d_model;
+  a.km = ctx->km;
+  if (host_params) std::memcpy(a.hp, params, np * sizeof(double));
+  else a.params = params;
   a.part = ctx->d_part;
   a.ld = ctx->num_sms;
   a.gram_store = ctx->d_gram;
   a.counter = ctx->d_counter;
-  a.err = ctx->d_err;
   a.rates = rates;
-  a.result = ctx->d_result;
+  a.result = result;
+  a.out_nll = out_nll;
+  a.out_grad = out_grad;
   a.sum_t = ctx->sum_t;
   a.inv_sum_w = ctx->inv_sum_w;
   a.trace = ctx->d_trace;
   if (full) {
     // Static, cost-balanced assignment of MC tiles to blocks: block q takes
     // data tiles q, q + grid, ... and MC tiles [range[q], range[q + 1]).
-    const int64_t n_dt = (ctx->data.dev.n + 255) / 256, n_mt = (ctx->mc.dev.n + 255) / 256;
+    const int64_t n_dt = ctx->data.dev.n_tiles, n_mt = ctx->mc.dev.n_tiles;
     if (ctx->ranges_key[0] != n_dt || ctx->ranges_key[1] != n_mt || ctx->ranges_key[2] != grid) {
       const int64_t R = ctx->f32 ? kDataTileCostF32 : kDataTileCostF64;
       const int64_t total = R * n_dt + n_mt, G = grid;
@@ -385,7 +391,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.mc_ranges = ctx->d_ranges;
 
   if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
-  TDMIX_CK(ctx->ops->eval(full, want_grad, grid, st, a, ctx->d_floating));
+  TDMIX_CK(ctx->ops->eval(full, want_grad, grid, st, a));
   if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 1))) return rc;
   if (full) {
     ctx->gram_valid = true;
@@ -420,33 +426,29 @@ cudaStream_t stream_of(tdmix_ctx* ctx) { return ctx->stream; }
 int num_sms_of(tdmix_ctx* ctx) { return ctx->num_sms; }
 const CompiledModel& model_of(tdmix_ctx* ctx) { return ctx->model; }
 const ShapeOps* ops_of(tdmix_ctx* ctx) { return ctx->ops; }
-const DevModel* dev_model_of(tdmix_ctx* ctx) { return ctx->d_model; }
-const int* dev_floating_of(tdmix_ctx* ctx) { return ctx->d_floating; }
+const ModelConst& model_const_of(tdmix_ctx* ctx) { return ctx->km; }
 bool is_f32(tdmix_ctx* ctx) { return ctx->f32; }
 double inv_sum_w_of(tdmix_ctx* ctx) { return ctx->inv_sum_w; }
 const double* gram_store_of(tdmix_ctx* ctx) { return ctx->d_gram; }
 std::string& error_of(tdmix_ctx* ctx) { return ctx->err; }
 
 // Computes the component cache of a data sample at host parameters `params`
-// (one full evaluation with the loaded MC) and hands its device buffers to
-// the caller: *cache ([2U][pitch] working precision), *t ([pitch] f64).
-int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* params, void** cache, double** t,
-                         int64_t* pitch, double* sum_t) {
+// (one full evaluation with the loaded MC) and hands its device buffer to
+// the caller: *cache (tile-major, SampleDev::cache), *tile_bytes per tile.
+int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* params, void** cache,
+                         int64_t* tile_bytes, double* sum_t) {
   int rc = load_sample(ctx, ev, true, ctx->data);
   if (rc) return rc;
   ctx->cache_valid = false;
-  if ((rc = enqueue_eval(ctx, params, true, false, nullptr))) return rc;
+  if ((rc = enqueue_eval(ctx, params, true, false, nullptr, ctx->d_result))) return rc;
   TDMIX_CK(cudaStreamSynchronize(ctx->stream));
   Sample& d = ctx->data;
   *cache = d.dev.cache;
-  *t = const_cast<double*>(d.dev.t);
-  *pitch = d.dev.pitch;
+  *tile_bytes = d.dev.cache_tile_bytes;
   *sum_t = ctx->sum_t;
-  // keep cache and t alive, free the planes and scratch
-  std::vector<void*> keep;
+  // keep the cache alive, free the planes and scratch
   for (void* p : d.owned)
-    if (p == d.dev.cache || p == d.dev.t) keep.push_back(p);
-    else cudaFree(p);
+    if (p != d.dev.cache) cudaFree(p);
   d.owned.clear();
   d = Sample{};
   ctx->cache_valid = false;
@@ -459,7 +461,7 @@ int compute_mc_totals(tdmix_ctx* ctx, const double* params, const tdmix_events* 
   int rc = load_sample(ctx, one_event, true, ctx->data);
   if (rc) return rc;
   ctx->cache_valid = false;
-  if ((rc = enqueue_eval(ctx, params, true, false, nullptr))) return rc;
+  if ((rc = enqueue_eval(ctx, params, true, false, nullptr, ctx->d_result))) return rc;
   TDMIX_CK(cudaStreamSynchronize(ctx->stream));
   free_sample(ctx->data);
   ctx->cache_valid = false;
@@ -495,24 +497,26 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   TDMIX_CK(cudaGetDevice(&ctx->device));
   TDMIX_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
   const int np = ctx->model.n_params();
+  {
+    const CompiledModel& m = ctx->model;
+    const int npl = (ctx->f32 ? 2 : 1) * m.NS() + m.NX() + m.U * m.NO;
+    if (npl != ctx->ops->n_planes || np > kMaxParams)
+      return fail(ctx, TDMIX_ERR_UNSUPPORTED, "model tables do not match the compiled specialisation");
+  }
   TDMIX_CK(cudaMalloc(&ctx->d_model, sizeof(DevModel)));
-  TDMIX_CK(cudaMalloc(&ctx->d_params, np * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_result, (kResHeader + np) * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_gram, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes) * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_sumt, sizeof(double)));
-  TDMIX_CK(cudaMalloc(&ctx->d_floating, np * sizeof(int)));
-  TDMIX_CK(cudaMalloc(&ctx->d_err, sizeof(int)));
-  TDMIX_CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
   TDMIX_CK(cudaMalloc(&ctx->d_part, size_t(ctx->num_sms) * (ctx->ops->mc_width + ctx->ops->data_width) * 8));
   TDMIX_CK(cudaMalloc(&ctx->d_counter, sizeof(unsigned)));
   TDMIX_CK(cudaMalloc(&ctx->d_ranges, (ctx->num_sms + 1) * sizeof(int64_t)));
   TDMIX_CK(cudaMemset(ctx->d_counter, 0, sizeof(unsigned)));
-  TDMIX_CK(cudaMallocHost(&ctx->h_params, np * sizeof(double)));
-  TDMIX_CK(cudaMallocHost(&ctx->h_result, (kResHeader + np) * sizeof(double)));
+  TDMIX_CK(cudaHostAlloc(&ctx->h_result, (kResHeader + np) * sizeof(double), cudaHostAllocMapped));
+  TDMIX_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->d_result_map), ctx->h_result, 0));
   DevModel dm = make_dev_model(ctx->model);
   TDMIX_CK(cudaMemcpy(ctx->d_model, &dm, sizeof dm, cudaMemcpyHostToDevice));
   ctx->floating = ctx->model.floating_mask();
-  TDMIX_CK(cudaMemcpy(ctx->d_floating, ctx->floating.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  ctx->km = make_model_const(ctx->model, ctx->floating);
   return TDMIX_OK;
 }
 
@@ -543,7 +547,7 @@ int tdmix_set_floating(tdmix_ctx* ctx, const int* mask) {
   if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
   const int np = ctx->model.n_params();
   for (int k = 0; k < np; ++k) ctx->floating[k] = mask[k] != 0;
-  TDMIX_CK(cudaMemcpy(ctx->d_floating, ctx->floating.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+  ctx->km = make_model_const(ctx->model, ctx->floating);
   return TDMIX_OK;
 }
 
@@ -569,21 +573,18 @@ int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* gra
     return fail(ctx, TDMIX_ERR_ARG, "nll_out and grad_out must both be host or both be device memory");
   int rc;
   if (host_params && (rc = check_params(ctx, params))) return rc;
-  if ((rc = enqueue_eval(ctx, params, host_params, grad_out != nullptr, nullptr))) return rc;
-  const int np = ctx->model.n_params();
   cudaStream_t st = ctx->stream;
+  const int np = ctx->model.n_params();
   if (host_out) {
-    TDMIX_CK(cudaMemcpyAsync(ctx->h_result, ctx->d_result, (kResHeader + np) * sizeof(double),
-                             cudaMemcpyDeviceToHost, st));
+    // the last block writes the result vector straight into mapped host memory
+    if ((rc = enqueue_eval(ctx, params, host_params, grad_out != nullptr, nullptr, ctx->d_result_map))) return rc;
     TDMIX_CK(cudaStreamSynchronize(st));
     *nll_out = ctx->h_result[0];
     if (grad_out) std::memcpy(grad_out, ctx->h_result + kResHeader, np * sizeof(double));
     return result_status(ctx);
   }
-  TDMIX_CK(cudaMemcpyAsync(nll_out, ctx->d_result, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  if (grad_out)
-    TDMIX_CK(cudaMemcpyAsync(grad_out, ctx->d_result + kResHeader, np * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  return TDMIX_OK;
+  // device outputs: written by the kernel itself, nothing else is enqueued
+  return enqueue_eval(ctx, params, host_params, grad_out != nullptr, nullptr, ctx->d_result, nll_out, grad_out);
 }
 
 int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, double* norm_out) {
@@ -595,7 +596,7 @@ int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, d
   if (host_params && (rc = check_params(ctx, params))) return rc;
   if (!ctx->data.loaded) return fail(ctx, TDMIX_ERR_STATE, "load data and MC events first");
   double* rates = host_out ? ctx->data.rates : rates_out;
-  if ((rc = enqueue_eval(ctx, params, host_params, false, rates))) return rc;
+  if ((rc = enqueue_eval(ctx, params, host_params, false, rates, ctx->d_result))) return rc;
   cudaStream_t st = ctx->stream;
   const int64_t n = ctx->data.dev.n;
   if (host_out) {
@@ -672,7 +673,6 @@ int tdmix_trace(tdmix_ctx* ctx, int enable) {
   } else if (!enable && ctx->d_trace) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->d_trace);
-  cudaFree(ctx->d_ranges);
     ctx->d_trace = nullptr;
   }
   return TDMIX_OK;
@@ -699,17 +699,13 @@ void tdmix_destroy(tdmix_ctx* ctx) {
   free_sample(ctx->data);
   free_sample(ctx->mc);
   cudaFree(ctx->d_model);
-  cudaFree(ctx->d_params);
   cudaFree(ctx->d_result);
   cudaFree(ctx->d_gram);
   cudaFree(ctx->d_sumt);
-  cudaFree(ctx->d_floating);
-  cudaFree(ctx->d_err);
   cudaFree(ctx->d_counter);
   cudaFree(ctx->d_part);
   cudaFree(ctx->d_trace);
   cudaFree(ctx->d_ranges);
-  if (ctx->h_params) cudaFreeHost(ctx->h_params);
   if (ctx->h_result) cudaFreeHost(ctx->h_result);
   for (int c = 0; c < TDMIX_PROF_CLASSES; ++c)
     for (int ph = 0; ph < 2; ++ph)

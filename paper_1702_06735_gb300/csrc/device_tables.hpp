@@ -23,29 +23,57 @@ struct DevModel {
   double xplane_ma[kMaxXPlanes], xplane_mb[kMaxXPlanes];
 };
 
-// Device view of one event sample (data or phase-space MC).
-struct SampleDev {
-  int64_t n, pitch;
-  void* s;            // invariants: fp64 [NS][pitch]; fp32 [2][NS][pitch] (hi, lo)
-  void* x;            // width factors X(s) [NX][pitch]
-  void* k;            // spin x barrier factors [U*NO][pitch]
-  const double* t;    // decay times (data)
-  const void* w;      // event weights (MC) or null
-  void* cache;        // per-event components [2][U][pitch] (data)
+// Model constants the likelihood kernels read, passed by value in the
+// kernel parameters (constant bank): the fields of the model that enter the
+// per-evaluation constants and the epilogue.
+constexpr int kMaxParams = 2 * kMaxChains + 2 * kMaxRes + 2;
+struct ModelConst {
+  int n_chains, n_params;
+  double r_res, gamma, tau;  // tau = 1 / gamma
+  double res_ma[kMaxRes], res_mb[kMaxRes];
+  int8_t res_shape[kMaxRes], res_L[kMaxRes];
+  int8_t chain_comp[kMaxChains], chain_amp[kMaxChains];
+  uint8_t floating[kMaxParams];
 };
 
-// Arguments of the fused evaluation kernel.
+// Events per tile: the unit of every bulk copy and of the static work
+// assignment; one event per consumer thread.
+constexpr int kTileEvents = 256;
+
+// Device view of one event sample (data or phase-space MC), tile-major: tile
+// q (events 256 q .. 256 q + 255) is one contiguous block, so one bulk copy
+// moves a whole tile.
+//   planes: per tile the precomputed event planes [NPL][256] in the working
+//           precision T (invariants: fp64 [NS]; fp32 hi [NS] then lo [NS];
+//           width factors X [NX]; spin x barrier factors K [U*NO]), then the
+//           256 decay times (f64, data) or the 256 weights (T, weighted MC)
+//   cache:  (data) per tile the components [2U][256] (T: re planes, then im
+//           planes), then the 256 decay times (f64)
+// The event slots of the last tile beyond n are zero.
+struct SampleDev {
+  int64_t n, n_tiles;
+  const void* planes;
+  int64_t tile_bytes;
+  void* cache;
+  int64_t cache_tile_bytes;
+  int weighted;
+};
+
+// Arguments of the fused evaluation kernel (passed as a grid constant).
 struct EvalArgs {
   SampleDev data, mc;
-  const double* params;
-  const DevModel* dm;
+  ModelConst km;
+  const double* params;       // device parameter vector, or null: hp holds it
+  double hp[kMaxParams];      // parameter vector by value (host callers)
   void* part;            // float2 [width][ld] double-float block partials (MC columns, then data columns)
   int64_t ld;            // leading dimension of part (>= grid)
   double* gram_store;    // MC column totals of the last pass that ran the MC tiles
-  unsigned* counter;     // blocks finished; returned to 0 by the last block
-  int* err;              // bounded-wait failures; read and cleared by the last block
+  unsigned* counter;     // blocks finished (low 16 bits) and blocks that timed out
+                         // (high bits); returned to 0 by the last block
   double* rates;         // optional: e^{-Gamma t} B per data event
   double* result;        // [nll, N, n_bad or status, sum ln B, grad...]
+  double* out_nll;       // optional second destination of the NLL
+  double* out_grad;      // optional second destination of the gradient
   double sum_t;
   double inv_sum_w;           // 1 / sum of MC weights (the MC event count when unweighted)
   unsigned long long* trace;  // optional: per block kTracePhases globaltimer stamps (ns)
@@ -67,9 +95,9 @@ constexpr int kServeMaxRequests = 1024;  // requests per batch at most
 
 // One request of a serving batch (see serve.cuh).
 struct ServeReq {
-  const void* cache;     // [2U][pitch] components (working precision)
-  const double* t;       // [pitch] decay times
-  int64_t n, pitch;
+  const void* cache;     // tile-major component cache with decay times (SampleDev::cache)
+  int64_t n;
+  int64_t tile_bytes;    // bytes of one cache tile
   int32_t chunk_begin;   // first row of this request in the partial array
   int32_t n_chunks;
   int32_t chunk_tiles;   // tiles per chunk (the last chunk may have fewer)
@@ -82,8 +110,7 @@ struct ServeArgs {
   int n_req;
   int total_chunks;
   const double* params;     // [n_req][n_params]
-  const DevModel* dm;
-  const int* floating;
+  ModelConst km;
   const double* mc_cols;    // MC column totals of the fixed model
   double inv_sum_w;
   void* part;               // float2 [total_chunks][WD] chunk partials

@@ -34,8 +34,19 @@ struct PrecF32 {
 
 template <class T>
 __device__ __forceinline__ T rcp(T v);
+// Hardware reciprocal approximation refined by two Newton-Raphson steps
+// r <- r + r (1 - v r): each step squares the relative error, so from the
+// approximation's ~2^-23 the result is within an ulp or two of 1/v (not
+// correctly rounded), for positive normal v.
 template <>
-__device__ __forceinline__ double rcp<double>(double v) { return __drcp_rn(v); }
+__device__ __forceinline__ double rcp<double>(double v) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+  double e = fma(-v, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-v, r, 1.0);
+  return fma(r, e, r);
+}
 // MUFU reciprocal refined by one Newton-Raphson step r + r (1 - v r):
 // relative error ~ (2^-22)^2 before the final rounding, i.e. within an ulp
 // of the correctly rounded reciprocal, for positive normal v.

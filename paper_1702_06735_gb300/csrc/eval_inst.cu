@@ -31,7 +31,7 @@ template <class S>
 struct Ops {
   static constexpr bool kOk = S::U <= kMaxRegisterGramU;
   template <bool FULL, bool GRAD, bool W>
-  static cudaError_t launch(int grid, cudaStream_t st, const EvalArgs& a, const int* floating) {
+  static cudaError_t launch(int grid, cudaStream_t st, const EvalArgs& a) {
     const int smem = Layout<Prec, S>::smem_bytes(FULL, int(a.ld));
     static int attr_set = 0;  // per instantiation: the largest size allowed so far
     if (smem > attr_set) {
@@ -40,17 +40,17 @@ struct Ops {
       if (e != cudaSuccess) return e;
       attr_set = smem;
     }
-    k_eval<Prec, S, FULL, GRAD, W><<<grid, kTile, smem, st>>>(a, floating);
+    k_eval<Prec, S, FULL, GRAD, W><<<grid, kTile, smem, st>>>(a);
     return cudaGetLastError();
   }
-  static cudaError_t eval(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a, const int* floating) {
+  static cudaError_t eval(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a) {
     if constexpr (kOk) {
-      const bool w = a.mc.w != nullptr;
+      const bool w = a.mc.weighted != 0;
       if (full) {
-        if (grad) return w ? launch<true, true, true>(grid, st, a, floating) : launch<true, true, false>(grid, st, a, floating);
-        return w ? launch<true, false, true>(grid, st, a, floating) : launch<true, false, false>(grid, st, a, floating);
+        if (grad) return w ? launch<true, true, true>(grid, st, a) : launch<true, true, false>(grid, st, a);
+        return w ? launch<true, false, true>(grid, st, a) : launch<true, false, false>(grid, st, a);
       }
-      return grad ? launch<false, true, false>(grid, st, a, floating) : launch<false, false, false>(grid, st, a, floating);
+      return grad ? launch<false, true, false>(grid, st, a) : launch<false, false, false>(grid, st, a);
     }
     return cudaErrorNotSupported;
   }
@@ -78,8 +78,10 @@ struct Ops {
 const ShapeOps* TDMIX_FIND(const std::string& sig) {
 #define TDMIX_SHAPE_ENTRY(S)                                                                  \
   if (Ops<shapes::S>::kOk && sig == shapes::S::sig()) {                                       \
-    static const ShapeOps o = {shapes::S::sig(), shapes::S::U, shapes::S::NR,                 \
-                               Layout<Prec, shapes::S>::WMC, Layout<Prec, shapes::S>::WD,     \
+    using LY_ = Layout<Prec, shapes::S>;                                                      \
+    static const ShapeOps o = {shapes::S::sig(), shapes::S::U, shapes::S::NR, LY_::WMC, LY_::WD, \
+                               LY_::NPL_FULL, LY_::data_tile_bytes(), LY_::mc_tile_bytes(false), \
+                               LY_::mc_tile_bytes(true), LY_::cache_tile_bytes(),               \
                                &Ops<shapes::S>::eval, &Ops<shapes::S>::serve};                \
     return &o;                                                                                \
   }

@@ -1,20 +1,24 @@
 // One persistent kernel per likelihood evaluation.
 //
-// Every block (one per SM):
-//   1. starts bulk asynchronous copies of its first two event tiles,
-//   2. derives the per-evaluation constants from the parameter vector
+// A block (one per SM) has eight warps, one event per thread.  Its event
+// tiles move global -> shared with one bulk copy per tile (tiles are
+// contiguous in memory) into a ring of stages; each stage completes on its
+// own mbarrier, and the last warp to release a stage (a shared-memory count)
+// issues the copy of the tile that refills it, so no block barrier is taken
+// per tile.  The block
+//   1. derives the per-evaluation constants from the parameter vector
 //      (lineshape constants, coefficients of each component in A_f and
-//      Abar_f, time-integral weights of the normalisation),
-//   3. processes its data tiles (tiles b, b + grid, ...): lineshapes and
+//      Abar_f, time-integral weights of the normalisation) while its first
+//      tiles are in flight,
+//   2. processes its data tiles (tiles b, b + grid, ...): lineshapes and
 //      components (or the stored component cache), Eq. (mix) in its
 //      factorised form in double precision, ln B and its adjoint,
-//   4. processes its MC tiles: components, the normalisation matrix
-//      I_jk = <a_j^* a_k> and the adjoint of the time-integrated rate,
-//   5. writes its partial sums; the last block to finish sums the partials
-//      of all blocks in a fixed order (double-float arithmetic) and forms
-//      N, the NLL and the gradient.
-// Tiles move global -> shared by cp.async.bulk completing on mbarriers, two
-// stages deep; every wait is bounded and reports TDMIX_ERR_TIMEOUT.
+//   3. processes its MC tiles: components, the normalisation matrix
+//      I_jk = <a_j^* a_k> and the adjoint of the time-integrated rate.
+// Each block then writes its partial sums; the last block to finish sums the
+// partials of all blocks in a fixed order (double-float arithmetic) and forms
+// N, the NLL and the gradient.  Every wait is bounded and reports
+// TDMIX_ERR_TIMEOUT.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,70 +30,94 @@
 
 namespace tdmix {
 
-constexpr int kTile = 256;
+constexpr int kTile = kTileEvents;
+constexpr int kWarps = kTile / 32;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
+constexpr int kStageBudget = 200 * 1024;     // shared memory for the tile ring
 
 // Per-evaluation constants in double precision (shared memory of a block).
 struct CtaConst {
-  double m0[kMaxRes], g0[kMaxRes], m2[kMaxRes], kappa[kMaxRes], dk_dm[kMaxRes], dk_dg[kMaxRes];
+  double m0[kMaxRes], g0[kMaxRes], m2[kMaxRes], kappa[kMaxRes];
+  double dlk_dm[kMaxRes], dlk_dg[kMaxRes];  // d ln kappa / d m0, d ln kappa / d Gamma0
   double cA[kMaxComp][2], cB[kMaxComp][2];
-  double x, y, gamma, alpha, beta, gc, dc, ia, ic;
-  int chain_comp[kMaxChains], chain_amp[kMaxChains], floating[kMaxChains * 2 + 2 * kMaxRes + 2];
+  double x, y, gamma, tau, alpha, beta, gc, dc, ia, ic;
+  int chain_comp[kMaxChains], chain_amp[kMaxChains], floating[kMaxParams];
   int nonfinite, domain;
 };
 
-__device__ inline double dlnF_dz_dev(int L, double z) {
-  if (L == 0) return 0.0;
-  if (L == 1) return -0.5 / (1.0 + z);
-  return -0.5 * (3.0 + 2.0 * z) / (9.0 + 3.0 * z + z * z);
+// d ln kappa / d m0 and d ln kappa / d Gamma0 of resonance r (gradient only):
+// ln kappa = 2 ln m0 + ln Gamma0 - (2L+1)/2 ln q0^2 - 2 ln F_L(z0), z0 = q0^2 r^2,
+// d q0^2 / d m0 = 2 m0 (u^2 - (ma^2 - mb^2)^2) / (4 u^2), u = m0^2, and
+// q0^2 = lambda / (4u), so 1 / (2 q0^2) = 2u / lambda.
+__device__ inline void kappa_log_derivatives(const ModelConst& km, int r, double m0, double g0, CtaConst& cc) {
+  const int shape = km.res_shape[r];
+  if (shape == SHAPE_CONST) {
+    cc.dlk_dm[r] = rcp<double>(m0);
+    cc.dlk_dg[r] = rcp<double>(g0);
+  } else if (shape == SHAPE_MDW) {
+    const int L = km.res_L[r];
+    const double r2 = km.r_res * km.r_res;
+    const double a = km.res_ma[r] * km.res_ma[r], b = km.res_mb[r] * km.res_mb[r];
+    const double u = m0 * m0;
+    const double iu = rcp<double>(u), im0 = m0 * iu;  // 1/u, 1/m0
+    const double lam = u * u + a * a + b * b - 2.0 * (u * a + u * b + a * b);
+    const double q02 = 0.25 * lam * iu;
+    const double z0 = q02 * r2;
+    const double dq2 = 0.5 * m0 * (u * u - (a - b) * (a - b)) * iu * iu;
+    const double dlnF = L == 0 ? 0.0 : (L == 1 ? -0.5 * rcp<double>(1.0 + z0)
+                                               : -0.5 * (3.0 + 2.0 * z0) * rcp<double>(9.0 + 3.0 * z0 + z0 * z0));
+    cc.dlk_dm[r] = 2.0 * im0 - (2 * L + 1) * dq2 * (2.0 * rcp<double>(lam)) * u - 2.0 * dlnF * r2 * dq2;
+    cc.dlk_dg[r] = rcp<double>(g0);
+  } else {
+    cc.dlk_dm[r] = cc.dlk_dg[r] = 0.0;
+  }
 }
 
-// Threads of the block in parallel: first every parameter and model table
-// entry is loaded into shared memory, then thread r derives resonance r's
-// constants, thread c places chain c's coefficient and two threads the
-// mixing weights.  m0 Gamma(s) = kappa X(s) with, for a mass-dependent
-// width, kappa = m0^2 Gamma0 / (q0^(2L+1) F_L(q0 r)^2); with
+// The kTile threads of a block in parallel: first the parameter vector
+// (device memory, or the kernel parameters when `dparams` is null) is loaded
+// into shared memory, then thread c places chain c's coefficient, thread
+// 64 + r derives resonance r's constants, threads 96, 97 the mixing weights
+// and, with RES_GRAD, thread 128 + r the log-derivatives of kappa_r.
+// m0 Gamma(s) = kappa X(s) with, for a mass-dependent width,
+// kappa = m0^2 Gamma0 / (q0^(2L+1) F_L(q0 r)^2); with
 // lambda = Kallen(m0^2, ma^2, mb^2) = 4 m0^2 q0^2 this is
 // kappa = 2 m0^3 Gamma0 G_L(z0) (4 m0^2)^L lambda^-(2L+1)/2, G_L = 1/F_L^2
 // (1, 1 + z, 9 + 3z + z^2), z0 = q0^2 r^2; a constant width has
-// kappa = m0 Gamma0.  Only one reciprocal square root and one division sit
-// on the dependent chain (double precision is slow to issue on this GPU).
-template <class T>
-__device__ inline void derive_constants(const double* __restrict__ params, const DevModel* __restrict__ dm,
-                                        const int* __restrict__ floating, CtaConst& cc, BlockConst<T>& bc) {
-  __shared__ double sp[kMaxChains * 2 + 2 * kMaxRes + 2];
-  __shared__ int s_nc, s_nr, s_u, s_np;
+// kappa = m0 Gamma0.  Only reciprocal square roots and Newton reciprocals
+// sit on the dependent chains (double precision is slow to issue on this
+// GPU).  Ends without a barrier: the caller synchronises.
+template <class T, int U, int NR, bool RES_GRAD = false>
+__device__ inline void derive_constants(const double* __restrict__ dparams, const double* hp, const ModelConst& km,
+                                        CtaConst& cc, BlockConst<T>& bc) {
+  __shared__ double sp[kMaxParams];
   const int tid = threadIdx.x;
+  const int nc = km.n_chains, np = km.n_params;
+  for (int k = tid; k < np; k += kTile) {
+    sp[k] = dparams ? dparams[k] : hp[k];
+    cc.floating[k] = km.floating[k];
+  }
+  for (int j = tid; j < U; j += kTile) cc.cA[j][0] = cc.cA[j][1] = cc.cB[j][0] = cc.cB[j][1] = 0.0;
+  for (int c = tid; c < nc; c += kTile) {
+    cc.chain_comp[c] = km.chain_comp[c];
+    cc.chain_amp[c] = km.chain_amp[c];
+  }
   if (tid == 0) {
-    s_nc = dm->n_chains;
-    s_nr = dm->NR;
-    s_u = dm->U;
-    s_np = dm->n_params;
     cc.nonfinite = cc.domain = 0;
-    cc.gamma = dm->gamma;
+    cc.gamma = km.gamma;
+    cc.tau = km.tau;
   }
   __syncthreads();
-  const int nc = s_nc, NR = s_nr, U = s_u, np = s_np;
-  for (int k = tid; k < np; k += blockDim.x) {
-    const double v = params[k];
-    sp[k] = v;
-    cc.floating[k] = floating[k];
-    if (!isfinite(v)) atomicOr(&cc.nonfinite, 1);
+  for (int k = tid; k < np; k += kTile)
+    if (!isfinite(sp[k])) atomicOr(&cc.nonfinite, 1);
+  if (tid < nc) {
+    double(*dst)[2] = cc.chain_amp[tid] == 0 ? cc.cA : cc.cB;
+    dst[cc.chain_comp[tid]][0] = sp[2 * tid];
+    dst[cc.chain_comp[tid]][1] = sp[2 * tid + 1];
   }
-  for (int j = tid; j < U; j += blockDim.x) cc.cA[j][0] = cc.cA[j][1] = cc.cB[j][0] = cc.cB[j][1] = 0.0;
-  for (int c = tid; c < nc; c += blockDim.x) {
-    cc.chain_comp[c] = dm->chain_comp[c];
-    cc.chain_amp[c] = dm->chain_amp[c];
-  }
-  __syncthreads();
-  for (int c = tid; c < nc; c += blockDim.x) {
-    double(*dst)[2] = cc.chain_amp[c] == 0 ? cc.cA : cc.cB;
-    dst[cc.chain_comp[c]][0] = sp[2 * c];
-    dst[cc.chain_comp[c]][1] = sp[2 * c + 1];
-  }
-  for (int r = tid; r < NR; r += blockDim.x) {
-    const int shape = dm->res_shape[r], L = dm->res_L[r];
-    const double ma = dm->res_ma[r], mb = dm->res_mb[r], rr = dm->r_res;
+  if (tid >= 64 && tid < 64 + NR) {
+    const int r = tid - 64;
+    const int shape = km.res_shape[r], L = km.res_L[r];
+    const double ma = km.res_ma[r], mb = km.res_mb[r], rr = km.r_res;
     const double m0 = sp[2 * nc + 2 * r], g0 = sp[2 * nc + 2 * r + 1];
     const double u = m0 * m0;
     double kap = 0;
@@ -100,9 +128,9 @@ __device__ inline void derive_constants(const double* __restrict__ params, const
       const double a2 = ma * ma, b2 = mb * mb;
       const double lam = u * u + a2 * a2 + b2 * b2 - 2.0 * (u * a2 + u * b2 + a2 * b2);
       if (!(lam > 0)) atomicOr(&cc.domain, 1);
-      const double rs = rsqrt(lam);                  // lambda^-1/2
-      const double z0 = lam * rr * rr / (4.0 * u);   // (q0 r)^2, off the rsqrt chain
-      double g = 1.0, w = rs;                        // G_L(z0) and lambda^-(2L+1)/2 (4u)^L
+      const double rs = rsqrt(lam);                                  // lambda^-1/2
+      const double z0 = lam * (0.25 * rr * rr) * rcp<double>(u);     // (q0 r)^2, off the rsqrt chain
+      double g = 1.0, w = rs;                                        // G_L(z0) and lambda^-(2L+1)/2 (4u)^L
       if (L == 1) {
         g = 1.0 + z0;
         w = rs * rs * rs * (4.0 * u);
@@ -128,15 +156,19 @@ __device__ inline void derive_constants(const double* __restrict__ params, const
     bc.kappa[r] = T(kap);
     bc.kappa_lo[r] = T(kap - double(T(kap)));
   }
-  // mixing weights: thread 32 and 33 each take one reciprocal
-  if (tid == 32 || tid == 33) {
+  if (RES_GRAD && tid >= 128 && tid < 128 + NR) {
+    const int r = tid - 128;
+    kappa_log_derivatives(km, r, sp[2 * nc + 2 * r], sp[2 * nc + 2 * r + 1], cc);
+  }
+  // mixing weights: 1/(1 - y^2) and 1/(1 + x^2) on two threads
+  if (tid == 96 || tid == 97) {
     const double x = sp[2 * nc + 2 * NR], y = sp[2 * nc + 2 * NR + 1];
-    if (tid == 32) {
+    if (tid == 96) {
       if (!(fabs(y) < 1.0)) atomicOr(&cc.domain, 1);
-      cc.ia = 1.0 / (1.0 - y * y);
+      cc.ia = rcp<double>(1.0 - y * y);
       cc.y = y;
     } else {
-      cc.ic = 1.0 / (1.0 + x * x);
+      cc.ic = rcp<double>(1.0 + x * x);
       cc.x = x;
     }
   }
@@ -155,7 +187,7 @@ __device__ inline void derive_constants(const double* __restrict__ params, const
     bc.gc = T(cc.gc);
     bc.dc = T(cc.dc);
   }
-  for (int j = tid; j < U; j += blockDim.x) {
+  for (int j = tid; j < U; j += kTile) {
     for (int q = 0; q < 2; ++q) {
       bc.cA[j][q] = T(cc.cA[j][q]);
       bc.cB[j][q] = T(cc.cB[j][q]);
@@ -195,120 +227,115 @@ struct Layout {
   static constexpr int W = WMC + WD;
   static constexpr int NPL_FULL = Planes<P, S>::W0;    // invariants, width factors, spin factors
   static constexpr int NPL_CACHE = 2 * U;             // component cache (re, im)
-  // bytes of one stage: planes, then one 8-byte-per-event plane (t or w)
+  // bytes of one stage: planes, then one 8-byte-per-event plane (t; the MC
+  // weights need at most as much)
   static constexpr int stage_bytes(bool full) {
     return (full ? NPL_FULL : NPL_CACHE) * kTile * int(sizeof(T)) + kTile * 8;
   }
-  // dynamic shared memory: two stages, reused by the last block for the
+  // ring depth: as many stages as fit the budget, 2 to 4
+  static constexpr int stages(bool full) {
+    const int n = kStageBudget / stage_bytes(full);
+    return n < 2 ? 2 : (n > 4 ? 4 : n);
+  }
+  // bytes of one tile in global memory (SampleDev::tile_bytes / cache_tile_bytes)
+  static constexpr int64_t data_tile_bytes() { return int64_t(NPL_FULL) * kTile * sizeof(T) + kTile * 8; }
+  static constexpr int64_t mc_tile_bytes(bool weighted) {
+    return int64_t(NPL_FULL) * kTile * sizeof(T) + (weighted ? kTile * sizeof(T) : 0);
+  }
+  static constexpr int64_t cache_tile_bytes() { return int64_t(NPL_CACHE) * kTile * sizeof(T) + kTile * 8; }
+  // dynamic shared memory: the stage ring, reused by the last block for the
   // partial array of `ld` blocks
   static constexpr int smem_bytes(bool full, int ld) {
-    const int st = 2 * stage_bytes(full), pa = W * ld * 8;
+    const int st = stages(full) * stage_bytes(full), pa = W * ld * 8;
     return st > pa ? st : pa;
   }
 };
 
-// dkappa/dm0 and dkappa/dGamma0 of resonance r (used for the gradient only):
-// ln kappa = 2 ln m0 + ln Gamma0 - (2L+1)/2 ln q0^2 - 2 ln F_L(z0), z0 = q0^2 r^2,
-// d q0^2 / d m0 = 2 m0 (u^2 - (ma^2 - mb^2)^2) / (4 u^2), u = m0^2.
-__device__ inline void kappa_derivatives(const DevModel* dm, int r, double m0, double g0, double kap, CtaConst& cc) {
-  const int shape = dm->res_shape[r];
-  if (shape == SHAPE_CONST) {
-    cc.dk_dm[r] = g0;
-    cc.dk_dg[r] = m0;
-  } else if (shape == SHAPE_MDW) {
-    const int L = dm->res_L[r];
-    const double r2 = dm->r_res * dm->r_res;
-    const double a = dm->res_ma[r] * dm->res_ma[r], b = dm->res_mb[r] * dm->res_mb[r];
-    const double u = m0 * m0;
-    const double q02 = breakup2(u, a, b);
-    const double z0 = q02 * r2;
-    const double dq2 = 2.0 * m0 * (u * u - (a - b) * (a - b)) / (4.0 * u * u);
-    const double dlnk = 2.0 / m0 - (2 * L + 1) * dq2 / (2.0 * q02) - 2.0 * dlnF_dz_dev(L, z0) * r2 * dq2;
-    cc.dk_dm[r] = kap * dlnk;
-    cc.dk_dg[r] = kap / g0;
-  } else {
-    cc.dk_dm[r] = cc.dk_dg[r] = 0.0;
-  }
-}
-
-// Last block: normalisation, NLL and gradient from the column totals.
+// Likelihood from the MC column totals `mcs` and the data column totals
+// `ds` of one sample: writes [nll, N, n_bad or status, sum ln B, grad...]
+// to `res` (and the NLL and gradient to `onll`, `og` when not null).
 //   N = <alpha |A|^2 + beta |Abar|^2 - 2 gc Re(A Abar*) - 2 dc Im(A Abar*)> / Gamma
 // is Eq. (mix) integrated over t in [0, inf) and averaged over the MC sample
 // (alpha = 1/(1-y^2) + 1/(1+x^2), beta = 1/(1-y^2) - 1/(1+x^2),
 // gc = y/(1-y^2), dc = x/(1+x^2)); with S_jk = sum_e w_e a_j^* a_k and
 // I = S / sum w: <|A|^2> = cA^H I cA, <|Abar|^2> = cB^H I cB,
 // <A Abar*> = cB^H I cA.   NLL = -sum ln B + Gamma sum t + N_d ln N.
-// Work is spread over threads so that only short chains of double-precision
-// operations are dependent; the logarithm runs on one thread while the
-// others form the gradient.
-// Likelihood from the MC column totals `mcs` and the data column totals
-// `ds` of one sample: writes [nll, N, n_bad or status, sum ln B, grad...]
-// to `res`.  Used by the last block of an evaluation and, in serving, by the
-// last chunk of each request.  `err` is a bounded-wait failure flag (read
-// and cleared).
+// Warps 0-3 form the four quadratic forms (one per warp, lanes over (j, k),
+// shuffle sum), warps 4-7 meanwhile the vectors S cA, S cB that the
+// coefficient gradient needs; then the logarithm runs on one thread while
+// the others form the gradient.  Used by the last block of an evaluation and,
+// in serving, by the last chunk of each request (at least 256 threads).
 template <class S>
-__device__ inline void finish_likelihood(double* res, int nc, int np, const CtaConst& cc, const double* mcs,
-                                         const double* ds, double Nd, double sum_t, double inv_sw, bool want_grad,
-                                         bool have_res_grad, int* err, unsigned long long* trace) {
+__device__ inline void finish_likelihood(double* res, double* onll, double* og, int nc, int np, const CtaConst& cc,
+                                         const double* mcs, const double* ds, double Nd, double sum_t, double inv_sw,
+                                         bool want_grad, bool have_res_grad, int timed_out,
+                                         unsigned long long* trace) {
   constexpr int U = S::U, NR = S::NR;
   constexpr int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2;
-  __shared__ double prod[2][U][U][2];
+  static_assert(2 * U <= 32, "S cA / S cB use four lanes per (which, j)");
   __shared__ double vv[2][U][2];  // S cA, S cB (unnormalised)
-  __shared__ double sh[8];        // AA, BB, Xr, Xi (unnormalised), nbar, sc
-  const int tid = threadIdx.x;
-  const int timed_out = *err;
+  __shared__ double sh[4];        // AA, BB, Xr, Xi (unnormalised)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int status = timed_out ? -7 : (cc.nonfinite ? -5 : (cc.domain ? -6 : 0));
   if (status != 0) {
-    __syncthreads();
-    if (tid == 0 && timed_out) *err = 0;
-    for (int k = tid; k < kResHeader + np; k += blockDim.x) res[k] = k == 2 ? double(status) : nan("");
+    for (int k = tid; k < kResHeader + np; k += blockDim.x) {
+      const double v = k == 2 ? double(status) : nan("");
+      res[k] = v;
+      if (k == 0 && onll) *onll = v;
+      if (k >= kResHeader && og) og[k - kResHeader] = v;
+    }
     return;
   }
-  // products S_jk c_k, thread (which, j, k)
-  for (int e = tid; e < 2 * U * U; e += blockDim.x) {
-    const int which = e / (U * U), j = (e / U) % U, k = e % U;
+  // S_jk (Hermitian) from the packed totals: Re over j <= k, Im over j < k
+  auto s_at = [&](int j, int k, double& sr, double& si) {
     const int lo = j < k ? j : k, hi = j < k ? k : j;
-    const int ire = lo * U - lo * (lo - 1) / 2 + (hi - lo);
-    const int iim = lo * (U - 1) - lo * (lo - 1) / 2 + (hi - lo - 1);
-    const double sr = mcs[1 + ire];
-    const double si = j == k ? 0.0 : (j < k ? mcs[1 + NRE + iim] : -mcs[1 + NRE + iim]);
-    const double cr = which ? cc.cB[k][0] : cc.cA[k][0], ci = which ? cc.cB[k][1] : cc.cA[k][1];
-    prod[which][j][k][0] = sr * cr - si * ci;
-    prod[which][j][k][1] = sr * ci + si * cr;
-  }
-  __syncthreads();
-  for (int e = tid; e < 2 * U; e += blockDim.x) {
-    const int which = e / U, j = e % U;
-    double re = 0, im = 0;
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      re += prod[which][j][k][0];
-      im += prod[which][j][k][1];
-    }
-    vv[which][j][0] = re;
-    vv[which][j][1] = im;
-  }
-  __syncthreads();
-  if (tid < 4) {
-    // tid 0: cA^H S cA, 1: cB^H S cB, 2/3: Re/Im cB^H S cA
-    const double(*c)[2] = tid == 0 ? cc.cA : cc.cB;
-    const int w = tid == 1 ? 1 : 0;
+    sr = mcs[1 + lo * U - lo * (lo - 1) / 2 + (hi - lo)];
+    si = j == k ? 0.0 : mcs[1 + NRE + lo * (U - 1) - lo * (lo - 1) / 2 + (hi - lo - 1)];
+    if (j > k) si = -si;
+  };
+  if (warp < 4) {
+    // warp 0: cA^H S cA, 1: cB^H S cB, 2 / 3: Re / Im cB^H S cA
+    const double(*cl)[2] = warp == 0 ? cc.cA : cc.cB;
+    const double(*cr)[2] = warp == 1 ? cc.cB : cc.cA;
     double acc = 0;
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      if (tid == 3) acc += c[j][0] * vv[w][j][1] - c[j][1] * vv[w][j][0];
-      else acc += c[j][0] * vv[w][j][0] + c[j][1] * vv[w][j][1];
+    for (int e = lane; e < U * U; e += 32) {
+      const int j = e / U, k = e % U;
+      double sr, si;
+      s_at(j, k, sr, si);
+      const double vr = sr * cr[k][0] - si * cr[k][1], vi = sr * cr[k][1] + si * cr[k][0];
+      acc += warp == 3 ? cl[j][0] * vi - cl[j][1] * vr : cl[j][0] * vr + cl[j][1] * vi;
     }
-    sh[tid] = acc;
+    acc = warp_sum(acc);
+    if (lane == 0) sh[warp] = acc;
+  } else if (warp < 8 && want_grad) {
+    // (which, j) = pair e / 4, k over residue e % 4; four lanes combined by shuffles
+    const int e = tid - 128, pr = e >> 2, q = e & 3;
+    const int which = pr / U, j = pr % U;
+    double re = 0, im = 0;
+    if (pr < 2 * U) {
+      const double(*c)[2] = which ? cc.cB : cc.cA;
+      for (int k = q; k < U; k += 4) {
+        double sr, si;
+        s_at(j, k, sr, si);
+        re += sr * c[k][0] - si * c[k][1];
+        im += sr * c[k][1] + si * c[k][0];
+      }
+    }
+    re += __shfl_xor_sync(0xffffffffu, re, 1);
+    im += __shfl_xor_sync(0xffffffffu, im, 1);
+    re += __shfl_xor_sync(0xffffffffu, re, 2);
+    im += __shfl_xor_sync(0xffffffffu, im, 2);
+    if (pr < 2 * U && q == 0) {
+      vv[which][j][0] = re;
+      vv[which][j][1] = im;
+    }
   }
   __syncthreads();
   const double al = cc.alpha, be = cc.beta, gc = cc.gc, dc = cc.dc, x = cc.x, y = cc.y, gamma = cc.gamma;
   const double AA = sh[0], BB = sh[1], Xr = sh[2], Xi = sh[3];
   const double nbar = (al * AA + be * BB - 2.0 * gc * Xr - 2.0 * dc * Xi) * inv_sw;
-  if (want_grad && tid == 32) sh[5] = Nd / nbar;  // d(N_d ln N) = N_d dnbar / nbar
-  __syncthreads();
   if (tid == 0) {
-    const double N = nbar / gamma;
+    const double N = nbar * cc.tau;
     const double sum_lnb = ds[0], nbad = ds[1];
     double nll = -sum_lnb + gamma * sum_t + Nd * log(N);
     if (nbad > 0 || !(N > 0)) nll = nan("");
@@ -316,15 +343,22 @@ __device__ inline void finish_likelihood(double* res, int nc, int np, const CtaC
     res[1] = N;
     res[2] = nbad;
     res[3] = sum_lnb;
-    if (timed_out) *err = 0;
+    if (onll) *onll = nll;
     if (trace) trace[6] = global_ns();
   }
   if (!want_grad) return;
-  const double sc = sh[5] * inv_sw;  // applied to unnormalised sensitivities
+  auto put = [&](int k, double v) {
+    res[kResHeader + k] = v;
+    if (og) og[k] = v;
+  };
+  // d(N_d ln N) = N_d dnbar / nbar, applied to unnormalised sensitivities
   // data columns: [sum ln B, n_bad, d/dx, d/dy, Re gA, Im gA, Re gB, Im gB, s1, s2]
   // chains on threads 32.., resonances on threads 160.., x and y on thread 224
   // (thread 0 is busy with the logarithm)
-  for (int ch = tid - 32; ch >= 0 && ch < nc; ch += blockDim.x) {
+  if (tid < 32) return;
+  const double sc = Nd * rcp<double>(nbar) * inv_sw;
+  if (tid - 32 < nc) {  // nc <= 64: threads 32 .. 95
+    const int ch = tid - 32;
     const int j = cc.chain_comp[ch];
     const double(*vA)[2] = vv[0];
     const double(*vB)[2] = vv[1];
@@ -341,24 +375,26 @@ __device__ inline void finish_likelihood(double* res, int nc, int np, const CtaC
       gi = ds[4 + 3 * U + j];
     }
     // d sum ln B / d Re c = 2 Re(g), d / d Im c = -2 Im(g)
-    res[kResHeader + 2 * ch] = cc.floating[2 * ch] ? -(2 * gr) + sc * dnr : 0.0;
-    res[kResHeader + 2 * ch + 1] = cc.floating[2 * ch + 1] ? 2 * gi + sc * dni : 0.0;
+    put(2 * ch, cc.floating[2 * ch] ? -(2 * gr) + sc * dnr : 0.0);
+    put(2 * ch + 1, cc.floating[2 * ch + 1] ? 2 * gi + sc * dni : 0.0);
   }
-  for (int r = tid - 160; r >= 0 && r < NR; r += blockDim.x) {
+  if (tid >= 160 && tid < 160 + NR) {
+    const int r = tid - 160;
     const double m0 = cc.m0[r];
     double dm_n = 0, dg_n = 0, dm_d = 0, dg_d = 0;
     if (have_res_grad) {
       // d n / d m0 = -4 m0 s1 - 2 dkappa/dm0 s2, d n / d Gamma0 = -2 dkappa/dGamma0 s2
+      const double dk_dm = cc.kappa[r] * cc.dlk_dm[r], dk_dg = cc.kappa[r] * cc.dlk_dg[r];
       const double s1m = mcs[1 + NRE + NIM + r], s2m = mcs[1 + NRE + NIM + NR + r];
-      dm_n = -4 * m0 * s1m - 2 * cc.dk_dm[r] * s2m;
-      dg_n = -2 * cc.dk_dg[r] * s2m;
+      dm_n = -4 * m0 * s1m - 2 * dk_dm * s2m;
+      dg_n = -2 * dk_dg * s2m;
       const double s1d = ds[4 + 4 * U + r], s2d = ds[4 + 4 * U + NR + r];
-      dm_d = -4 * m0 * s1d - 2 * cc.dk_dm[r] * s2d;
-      dg_d = -2 * cc.dk_dg[r] * s2d;
+      dm_d = -4 * m0 * s1d - 2 * dk_dm * s2d;
+      dg_d = -2 * dk_dg * s2d;
     }
     const int k = 2 * nc + 2 * r;
-    res[kResHeader + k] = cc.floating[k] ? -dm_d + sc * dm_n : 0.0;
-    res[kResHeader + k + 1] = cc.floating[k + 1] ? -dg_d + sc * dg_n : 0.0;
+    put(k, cc.floating[k] ? -dm_d + sc * dm_n : 0.0);
+    put(k + 1, cc.floating[k + 1] ? -dg_d + sc * dg_n : 0.0);
   }
   if (tid == 224) {
     const double ia = cc.ia, ic = cc.ic;
@@ -368,370 +404,380 @@ __device__ inline void finish_likelihood(double* res, int nc, int np, const CtaC
     const double dn_dx = dal_dx * AA + dbe_dx * BB - 2 * ddc_dx * Xi;
     const double dn_dy = dal_dy * AA + dbe_dy * BB - 2 * dgc_dy * Xr;
     const int k = 2 * nc + 2 * NR;
-    res[kResHeader + k] = cc.floating[k] ? -ds[2] + sc * dn_dx : 0.0;
-    res[kResHeader + k + 1] = cc.floating[k + 1] ? -ds[3] + sc * dn_dy : 0.0;
+    put(k, cc.floating[k] ? -ds[2] + sc * dn_dx : 0.0);
+    put(k + 1, cc.floating[k + 1] ? -ds[3] + sc * dn_dy : 0.0);
   }
 }
 
-template <class S>
-__device__ inline void final_epilogue(const EvalArgs& a, CtaConst& cc, const double* colsum, bool want_grad,
-                                      bool have_res_grad, unsigned long long* trace) {
-  constexpr int WMC = Layout<PrecF64, S>::WMC;
-  finish_likelihood<S>(a.result, a.dm->n_chains, a.dm->n_params, cc, colsum, colsum + WMC, double(a.data.n),
-                       a.sum_t, a.inv_sum_w, want_grad, have_res_grad, a.err, trace);
-}
-
 template <class P, class S, bool FULL, bool GRAD, bool WEIGHTED>
-__global__ void __launch_bounds__(kTile, 1) k_eval(EvalArgs a, const int* __restrict__ floating) {
+__global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalArgs a) {
   using T = typename P::T;
   using LY = Layout<P, S>;
-  using PL = Planes<P, S>;
   constexpr int U = S::U, NR = S::NR, NRE = LY::NRE, NIM = LY::NIM, WMC = LY::WMC, WD = LY::WD;
   constexpr int NPL = FULL ? LY::NPL_FULL : LY::NPL_CACHE;
+  constexpr int NST = LY::stages(FULL);
+  constexpr int STB = LY::stage_bytes(FULL);
   constexpr int TE = kTile;
   constexpr int ES = int(sizeof(T));
+  static_assert(NR <= 32 && kMaxChains <= 64, "thread roles of derive_constants");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[3];
+  __shared__ __align__(8) uint64_t full_bar[NST], part_bar;
+  __shared__ unsigned released[NST];  // warps done with the stage's current tile
+  __shared__ unsigned s_issued;       // items whose copy has been issued
   __shared__ CtaConst cc;
   __shared__ BlockConst<T> bc;
-  __shared__ double red[kTile / 32][WMC > WD ? WMC : WD];
+  __shared__ double red[kWarps][WMC > WD ? WMC : WD];
   __shared__ double colsum[LY::W];
-  __shared__ unsigned is_last;
+  __shared__ unsigned s_last, s_timeout;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   unsigned long long* trace = a.trace ? a.trace + size_t(blockIdx.x) * kTracePhases : nullptr;
   if (trace && tid == 0) trace[0] = global_ns();
   const SampleDev& dd = a.data;
   const SampleDev& dmc = a.mc;
-  const int64_t n_dt = (dd.n + TE - 1) / TE;
-  const int64_t n_mt = FULL ? (dmc.n + TE - 1) / TE : 0;
   // Block b takes data tiles b, b + G, ... and then the contiguous range of
   // MC tiles mc_ranges[b] .. mc_ranges[b + 1], chosen on the host so that
   // every block carries about the same cost.  The assignment depends only on
   // the sizes and the grid, so every run sums in the same order.
   const int64_t b = blockIdx.x;
+  const int64_t n_dt = dd.n_tiles;
   const int64_t my_data = n_dt > b ? (n_dt - 1 - b) / G + 1 : 0;
   const int64_t mc_begin = FULL ? a.mc_ranges[b] : 0, mc_end = FULL ? a.mc_ranges[b + 1] : 0;
   const int64_t my_items = my_data + (mc_end - mc_begin);
-  const int stage_bytes = LY::stage_bytes(FULL);
-  unsigned char* stage[2] = {smem_raw, smem_raw + stage_bytes};
 
-  // ---- bulk copies of one work item into a stage
+  // ---- one bulk copy of work item k (a whole tile) into stage k % NST
   auto issue = [&](int64_t k) {
-    const int st = int(k & 1);
-    const bool is_data = k < my_data;
-    const SampleDev& s = is_data ? dd : dmc;
-    const int64_t off = (is_data ? b + k * G : mc_begin + (k - my_data)) * TE;
-    uint32_t bytes = uint32_t(NPL) * TE * ES;
-    const bool extra = is_data || WEIGHTED;
-    if (extra) bytes += is_data ? TE * 8 : TE * ES;
-    mbar_arrive_expect_tx(&bars[st], bytes);
-    T* dst = reinterpret_cast<T*>(stage[st]);
-    for (int p = 0; p < NPL; ++p) {
-      const T* src;
+    const int st = int(k % NST);
+    const void* src;
+    uint32_t bytes;
+    if (k < my_data) {
+      const int64_t tile = b + k * G;
       if constexpr (FULL) {
-        if (p < PL::X0) src = static_cast<const T*>(s.s) + p * s.pitch;
-        else if (p < PL::K0) src = static_cast<const T*>(s.x) + (p - PL::X0) * s.pitch;
-        else src = static_cast<const T*>(s.k) + (p - PL::K0) * s.pitch;
+        src = static_cast<const unsigned char*>(dd.planes) + tile * dd.tile_bytes;
+        bytes = uint32_t(dd.tile_bytes);
       } else {
-        src = static_cast<const T*>(s.cache) + p * s.pitch;
+        src = static_cast<const unsigned char*>(dd.cache) + tile * dd.cache_tile_bytes;
+        bytes = uint32_t(dd.cache_tile_bytes);
       }
-      bulk_g2s(dst + p * TE, src + off, TE * ES, &bars[st]);
+    } else {
+      const int64_t tile = mc_begin + (k - my_data);
+      src = static_cast<const unsigned char*>(dmc.planes) + tile * dmc.tile_bytes;
+      bytes = uint32_t(dmc.tile_bytes);
     }
-    unsigned char* ex = stage[st] + NPL * TE * ES;
-    if (is_data) bulk_g2s(ex, dd.t + off, TE * 8, &bars[st]);
-    else if (WEIGHTED) bulk_g2s(ex, static_cast<const T*>(dmc.w) + off, TE * ES, &bars[st]);
+    mbar_arrive_expect_tx(&full_bar[st], bytes);
+    bulk_g2s(smem_raw + st * STB, src, bytes, &full_bar[st]);
   };
 
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full_bar[s], 1);
+      released[s] = 0;
+    }
+    mbar_init(&part_bar, 1);
     mbar_fence_init();
+    const int64_t first = my_items < NST ? my_items : NST;
+    for (int64_t k = 0; k < first; ++k) issue(k);
+    s_issued = unsigned(first);
   }
-  __syncthreads();
-  if (tid == 0) {
-    if (my_items > 0) issue(0);
-    if (my_items > 1) issue(1);
-  }
-  derive_constants<T>(a.params, a.dm, floating, cc, bc);
+  if (!FULL)  // stored MC totals of the fixed lineshapes
+    for (int v = tid; v < WMC; v += kTile) colsum[v] = a.gram_store[v];
+  derive_constants<T, U, NR, GRAD && FULL>(a.params, a.hp, a.km, cc, bc);
   __syncthreads();
   if (trace && tid == 0) trace[1] = global_ns();
 
-  int64_t k = 0;
   bool timed_out = false;
-
-  // ---- data tiles
-  {
-    double lnb = 0.0;
-    int bad = 0;
-    T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
-#pragma unroll
-    for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
-#pragma unroll
-    for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
-    T* cache = static_cast<T*>(dd.cache);
-    for (; k < my_data; ++k) {
-      const int64_t item = b + k * G;
-      const int st = int(k & 1);
-      const bool ok = mbar_wait_bounded(&bars[st], uint32_t((k >> 1) & 1), kWaitNs);
-      if (__syncthreads_or(!ok)) {
-        timed_out = true;
-        break;
-      }
-      const int64_t i = item * TE + tid;
-      if (i < dd.n) {
-        const T* sbase = reinterpret_cast<const T*>(stage[st]);
-        const double t_e = reinterpret_cast<const double*>(stage[st] + NPL * TE * ES)[tid];
-        const SmemSrc<P, S, TE> src{sbase, tid, false};
-        EventCore<P, S> ev;
-        if constexpr (FULL) {
-          ev.lineshapes(src, bc);
-          ev.components(src);
-#pragma unroll
-          for (int j = 0; j < U; ++j) {
-            cache[j * dd.pitch + i] = ev.ar[j];
-            cache[(U + j) * dd.pitch + i] = ev.ai[j];
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < U; ++j) {
-            ev.ar[j] = sbase[j * TE + tid];
-            ev.ai[j] = sbase[(U + j) * TE + tid];
-          }
+  uint32_t st = 0, ph = 0;
+  int64_t k = 0;
+  // This warp is done with item k (stage st).  The last of the eight warps
+  // to get here issues the copy of item k + NST into the same stage; the
+  // count is reset before that copy is issued, and a warp adds to it again
+  // only after the copy has completed on the stage's barrier.
+  auto release = [&]() {
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&released[st], 1u) == kWarps - 1) {
+        __threadfence_block();
+        released[st] = 0;
+        if (k + NST < my_items) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(k + NST);
+          atomicMax(&s_issued, unsigned(k + NST + 1));
         }
-        T Ar_, Ai_, Br_, Bi_;
-        ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
-        // Eq. (mix) as 2 |cosh(w) A - sinh(w) Abar|^2, w = (y + i x) Gamma t / 2, in double.
-        const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
-        const double gt = bc.gamma * t_e;
-        double cha, sha, cb, sb;
-        mixing_trig(0.5 * bc.y * gt, 0.5 * bc.x * gt, cha, sha, cb, sb);
-        const double chr = cha * cb, chi = sha * sb;  // cosh(w)
-        const double shr = sha * cb, shi = cha * sb;  // sinh(w)
-        const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);
-        const double Zi = chr * Ai + chi * Ar - (shr * Bi + shi * Br);
-        const double z2 = Zr * Zr + Zi * Zi;
-        const double B = 2.0 * z2;
-        if (a.rates) a.rates[i] = exp(-gt) * B;
-        if (B > 0.0 && B < INFINITY) {
-          lnb += log(B);
-          if constexpr (GRAD) {
-            // d ln B = 2 Re(V dZ), V = Z* / |Z|^2; dZ = cosh(w) dA - sinh(w) dAbar
-            // + (sinh(w) A - cosh(w) Abar) dw; dw/dy = Gamma t / 2, dw/dx = i Gamma t / 2.
-            // The sensitivities are formed in the working precision; in fp32
-            // cosh(w), sinh(w) and Z are re-derived in fp32 rather than
-            // converted from their fp64 values.
-            T cr, ci, sr, si, Zrt, Zit;
-            if constexpr (P::kF32) {
-              const float gtf = float(bc.gamma) * float(t_e);
-              float chf, shf, cbf, sbf;
-              mixing_trig_f32(0.5f * float(bc.y) * gtf, 0.5f * float(bc.x) * gtf, chf, shf, cbf, sbf);
-              cr = chf * cbf; ci = shf * sbf; sr = shf * cbf; si = chf * sbf;
-              Zrt = 0; Zit = 0;
-              cmac(Zrt, Zit, cr, ci, Ar_, Ai_);
-              cmac(Zrt, Zit, -sr, -si, Br_, Bi_);
-            } else {
-              cr = chr; ci = chi; sr = shr; si = shi;
-              Zrt = Zr; Zit = Zi;
-            }
-            const T iz = rcp<T>(fma(Zrt, Zrt, Zit * Zit));
-            const T Vr = Zrt * iz, Vi = -Zit * iz;
-            const T tAr = fma(Vr, cr, -Vi * ci), tAi = fma(Vr, ci, Vi * cr);
-            const T tBr = -fma(Vr, sr, -Vi * si), tBi = -fma(Vr, si, Vi * sr);
-            T Dr = 0, Di = 0;
-            cmac(Dr, Di, sr, si, Ar_, Ai_);
-            cmac(Dr, Di, -cr, -ci, Br_, Bi_);
-            const T tg = P::kF32 ? T(float(bc.gamma) * float(t_e)) : T(gt);
-            gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
-            gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
+      }
+    }
+    if (++st == NST) {
+      st = 0;
+      ph ^= 1u;
+    }
+  };
+
+  {
+    // ---- data tiles
+    {
+      double lnb = 0.0;
+      int bad = 0;
+      T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
+#pragma unroll
+      for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
+#pragma unroll
+      for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
+      for (; k < my_data; ++k) {
+        const int64_t tile = b + k * G;
+        const bool ok = mbar_wait_bounded(&full_bar[st], ph, kWaitNs);
+        if (__any_sync(0xffffffffu, !ok)) {
+          timed_out = true;
+          break;
+        }
+        const int64_t i = tile * TE + tid;
+        if (i < dd.n) {
+          const unsigned char* stage = smem_raw + st * STB;
+          const T* sbase = reinterpret_cast<const T*>(stage);
+          const double t_e = reinterpret_cast<const double*>(stage + NPL * TE * ES)[tid];
+          const SmemSrc<P, S, TE> src{sbase, tid, false};
+          EventCore<P, S> ev;
+          if constexpr (FULL) {
+            ev.lineshapes(src, bc);
+            ev.components(src);
+            T* cache = reinterpret_cast<T*>(static_cast<unsigned char*>(dd.cache) + tile * dd.cache_tile_bytes);
 #pragma unroll
             for (int j = 0; j < U; ++j) {
-              cmac(gAr[j], gAi[j], tAr, tAi, ev.ar[j], ev.ai[j]);
-              cmac(gBr[j], gBi[j], tBr, tBi, ev.ar[j], ev.ai[j]);
+              cache[j * TE + tid] = ev.ar[j];
+              cache[(U + j) * TE + tid] = ev.ai[j];
             }
-            if constexpr (FULL) ev.template backprop_lineshapes<false>(src, bc, tAr, tAi, tBr, tBi, T(1), s1, s2);
-          }
-        } else {
-          bad += 1;
-        }
-      }
-      __syncthreads();  // stage consumed
-      if (tid == 0 && k + 2 < my_items) issue(k + 2);
-    }
-    // block sum of the data accumulators -> colsum[WMC ..]
-    const int lane = tid & 31, warp = tid >> 5;
-    {
-      const double v0 = warp_sum(lnb), v1 = warp_sum(double(bad));
-      if (lane == 0) {
-        red[warp][0] = v0;
-        red[warp][1] = v1;
-      }
-    }
-    T vt[WD - 2];
-    vt[0] = gx;
-    vt[1] = gy;
+          } else {
 #pragma unroll
-    for (int j = 0; j < U; ++j) {
-      vt[2 + j] = gAr[j];
-      vt[2 + U + j] = gAi[j];
-      vt[2 + 2 * U + j] = gBr[j];
-      vt[2 + 3 * U + j] = gBi[j];
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      vt[2 + 4 * U + r] = s1[r];
-      vt[2 + 4 * U + NR + r] = s2[r];
-    }
-#pragma unroll
-    for (int q = 0; q < WD - 2; ++q) {
-      const T s = warp_sum(vt[q]);
-      if (lane == 0) red[warp][2 + q] = double(s);
-    }
-    __syncthreads();
-    for (int v = tid; v < WD; v += blockDim.x) {
-      double s = 0;
-      for (int w = 0; w < kTile / 32; ++w) s += red[w][v];
-      colsum[WMC + v] = s;
-    }
-    __syncthreads();
-  }
-
-  if (trace && tid == 0) trace[2] = global_ns();
-
-  // ---- MC tiles
-  if constexpr (FULL) {
-    T sw = 0, gre[NRE], gim[NIM > 0 ? NIM : 1], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
-#pragma unroll
-    for (int q = 0; q < NRE; ++q) gre[q] = 0;
-#pragma unroll
-    for (int q = 0; q < (NIM > 0 ? NIM : 1); ++q) gim[q] = 0;
-#pragma unroll
-    for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
-    for (; k < my_items && !timed_out; ++k) {
-      const int64_t item = mc_begin + (k - my_data);
-      const int st = int(k & 1);
-      const bool ok = mbar_wait_bounded(&bars[st], uint32_t((k >> 1) & 1), kWaitNs);
-      if (__syncthreads_or(!ok)) {
-        timed_out = true;
-        break;
-      }
-      const int64_t i = item * TE + tid;
-      if (i < dmc.n) {
-        const T* sbase = reinterpret_cast<const T*>(stage[st]);
-        const SmemSrc<P, S, TE> src{sbase, tid, false};
-        EventCore<P, S> ev;
-        ev.lineshapes(src, bc);
-        ev.components(src);
-        const T w = WEIGHTED ? reinterpret_cast<const T*>(stage[st] + NPL * TE * ES)[tid] : T(1);
-        sw += w;
-        int kr = 0, ki = 0;
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-          const T wr = WEIGHTED ? w * ev.ar[j] : ev.ar[j], wi = WEIGHTED ? w * ev.ai[j] : ev.ai[j];
-#pragma unroll
-          for (int kk = j; kk < U; ++kk) {
-            gre[kr] = fma(wr, ev.ar[kk], gre[kr]);
-            gre[kr] = fma(wi, ev.ai[kk], gre[kr]);
-            ++kr;
-            if (kk > j) {
-              gim[ki] = fma(wr, ev.ai[kk], gim[ki]);
-              gim[ki] = fma(-wi, ev.ar[kk], gim[ki]);
-              ++ki;
+            for (int j = 0; j < U; ++j) {
+              ev.ar[j] = sbase[j * TE + tid];
+              ev.ai[j] = sbase[(U + j) * TE + tid];
             }
           }
+          T Ar_, Ai_, Br_, Bi_;
+          ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
+          // Eq. (mix) as 2 |cosh(w) A - sinh(w) Abar|^2, w = (y + i x) Gamma t / 2, in double.
+          const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
+          const double gt = bc.gamma * t_e;
+          double cha, sha, cb, sb;
+          mixing_trig(0.5 * bc.y * gt, 0.5 * bc.x * gt, cha, sha, cb, sb);
+          const double chr = cha * cb, chi = sha * sb;  // cosh(w)
+          const double shr = sha * cb, shi = cha * sb;  // sinh(w)
+          const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);
+          const double Zi = chr * Ai + chi * Ar - (shr * Bi + shi * Br);
+          const double z2 = Zr * Zr + Zi * Zi;
+          const double B = 2.0 * z2;
+          if (a.rates) a.rates[i] = exp(-gt) * B;
+          if (B > 0.0 && B < INFINITY) {
+            lnb += log(B);
+            if constexpr (GRAD) {
+              // d ln B = 2 Re(V dZ), V = Z* / |Z|^2; dZ = cosh(w) dA - sinh(w) dAbar
+              // + (sinh(w) A - cosh(w) Abar) dw; dw/dy = Gamma t / 2, dw/dx = i Gamma t / 2.
+              // The sensitivities are formed in the working precision; in fp32
+              // cosh(w), sinh(w) and Z are re-derived in fp32 rather than
+              // converted from their fp64 values.
+              T cr, ci, sr, si, Zrt, Zit;
+              if constexpr (P::kF32) {
+                const float gtf = float(bc.gamma) * float(t_e);
+                float chf, shf, cbf, sbf;
+                mixing_trig_f32(0.5f * float(bc.y) * gtf, 0.5f * float(bc.x) * gtf, chf, shf, cbf, sbf);
+                cr = chf * cbf; ci = shf * sbf; sr = shf * cbf; si = chf * sbf;
+                Zrt = 0; Zit = 0;
+                cmac(Zrt, Zit, cr, ci, Ar_, Ai_);
+                cmac(Zrt, Zit, -sr, -si, Br_, Bi_);
+              } else {
+                cr = chr; ci = chi; sr = shr; si = shi;
+                Zrt = Zr; Zit = Zi;
+              }
+              const T iz = rcp<T>(fma(Zrt, Zrt, Zit * Zit));
+              const T Vr = Zrt * iz, Vi = -Zit * iz;
+              const T tAr = fma(Vr, cr, -Vi * ci), tAi = fma(Vr, ci, Vi * cr);
+              const T tBr = -fma(Vr, sr, -Vi * si), tBi = -fma(Vr, si, Vi * sr);
+              T Dr = 0, Di = 0;
+              cmac(Dr, Di, sr, si, Ar_, Ai_);
+              cmac(Dr, Di, -cr, -ci, Br_, Bi_);
+              const T tg = P::kF32 ? T(float(bc.gamma) * float(t_e)) : T(gt);
+              gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
+              gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
+#pragma unroll
+              for (int j = 0; j < U; ++j) {
+                cmac(gAr[j], gAi[j], tAr, tAi, ev.ar[j], ev.ai[j]);
+                cmac(gBr[j], gBi[j], tBr, tBi, ev.ar[j], ev.ai[j]);
+              }
+              if constexpr (FULL) ev.template backprop_lineshapes<false>(src, bc, tAr, tAi, tBr, tBi, T(1), s1, s2);
+            }
+          } else {
+            bad += 1;
+          }
         }
-        if constexpr (GRAD) {
-          T Ar, Ai, Br, Bi;
-          ev.amplitudes(bc, Ar, Ai, Br, Bi);
-          // n = alpha|A|^2 + beta|Abar|^2 - 2 gc Re(A Abar*) - 2 dc Im(A Abar*);
-          // dn = 2 Re(uA dA + uB dAbar), uA = alpha A* - (gc - i dc) Abar*,
-          // uB = beta Abar* - (gc + i dc) A*.
-          const T uAr = bc.alpha * Ar - bc.gc * Br + bc.dc * Bi;
-          const T uAi = -bc.alpha * Ai + bc.gc * Bi + bc.dc * Br;
-          const T uBr = bc.beta * Br - bc.gc * Ar - bc.dc * Ai;
-          const T uBi = -bc.beta * Bi + bc.gc * Ai - bc.dc * Ar;
-          ev.template backprop_lineshapes<WEIGHTED>(src, bc, uAr, uAi, uBr, uBi, w, s1, s2);
+        release();
+      }
+      // block sum of the data accumulators -> colsum[WMC ..]
+      {
+        const double v0 = warp_sum(lnb), v1 = warp_sum(double(bad));
+        if (lane == 0) {
+          red[warp][0] = v0;
+          red[warp][1] = v1;
         }
+      }
+      T vt[WD - 2];
+      vt[0] = gx;
+      vt[1] = gy;
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        vt[2 + j] = gAr[j];
+        vt[2 + U + j] = gAi[j];
+        vt[2 + 2 * U + j] = gBr[j];
+        vt[2 + 3 * U + j] = gBi[j];
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        vt[2 + 4 * U + r] = s1[r];
+        vt[2 + 4 * U + NR + r] = s2[r];
+      }
+#pragma unroll
+      for (int q = 0; q < WD - 2; ++q) {
+        const T s = warp_sum(vt[q]);
+        if (lane == 0) red[warp][2 + q] = double(s);
       }
       __syncthreads();
-      if (tid == 0 && k + 2 < my_items) issue(k + 2);
+      for (int v = tid; v < WD; v += kTile) {
+        double s = 0;
+        for (int w = 0; w < kWarps; ++w) s += red[w][v];
+        colsum[WMC + v] = s;
+      }
+      __syncthreads();
     }
-    const int lane = tid & 31, warp = tid >> 5;
-    T vt[WMC];
-    vt[0] = sw;
+    if (trace && tid == 0) trace[2] = global_ns();
+
+    // ---- MC tiles
+    if constexpr (FULL) {
+      T sw = 0, gre[NRE], gim[NIM > 0 ? NIM : 1], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
 #pragma unroll
-    for (int q = 0; q < NRE; ++q) vt[1 + q] = gre[q];
+      for (int q = 0; q < NRE; ++q) gre[q] = 0;
 #pragma unroll
-    for (int q = 0; q < NIM; ++q) vt[1 + NRE + q] = gim[q];
+      for (int q = 0; q < (NIM > 0 ? NIM : 1); ++q) gim[q] = 0;
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      vt[1 + NRE + NIM + r] = s1[r];
-      vt[1 + NRE + NIM + NR + r] = s2[r];
+      for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
+      for (; k < my_items && !timed_out; ++k) {
+        const int64_t tile = mc_begin + (k - my_data);
+        const bool ok = mbar_wait_bounded(&full_bar[st], ph, kWaitNs);
+        if (__any_sync(0xffffffffu, !ok)) {
+          timed_out = true;
+          break;
+        }
+        const int64_t i = tile * TE + tid;
+        if (i < dmc.n) {
+          const unsigned char* stage = smem_raw + st * STB;
+          const T* sbase = reinterpret_cast<const T*>(stage);
+          const SmemSrc<P, S, TE> src{sbase, tid, false};
+          EventCore<P, S> ev;
+          ev.lineshapes(src, bc);
+          ev.components(src);
+          const T w = WEIGHTED ? reinterpret_cast<const T*>(stage + NPL * TE * ES)[tid] : T(1);
+          sw += w;
+          int kr = 0, ki = 0;
+#pragma unroll
+          for (int j = 0; j < U; ++j) {
+            const T wr = WEIGHTED ? w * ev.ar[j] : ev.ar[j], wi = WEIGHTED ? w * ev.ai[j] : ev.ai[j];
+#pragma unroll
+            for (int kk = j; kk < U; ++kk) {
+              gre[kr] = fma(wr, ev.ar[kk], gre[kr]);
+              gre[kr] = fma(wi, ev.ai[kk], gre[kr]);
+              ++kr;
+              if (kk > j) {
+                gim[ki] = fma(wr, ev.ai[kk], gim[ki]);
+                gim[ki] = fma(-wi, ev.ar[kk], gim[ki]);
+                ++ki;
+              }
+            }
+          }
+          if constexpr (GRAD) {
+            T Ar, Ai, Br, Bi;
+            ev.amplitudes(bc, Ar, Ai, Br, Bi);
+            // n = alpha|A|^2 + beta|Abar|^2 - 2 gc Re(A Abar*) - 2 dc Im(A Abar*);
+            // dn = 2 Re(uA dA + uB dAbar), uA = alpha A* - (gc - i dc) Abar*,
+            // uB = beta Abar* - (gc + i dc) A*.
+            const T uAr = bc.alpha * Ar - bc.gc * Br + bc.dc * Bi;
+            const T uAi = -bc.alpha * Ai + bc.gc * Bi + bc.dc * Br;
+            const T uBr = bc.beta * Br - bc.gc * Ar - bc.dc * Ai;
+            const T uBi = -bc.beta * Bi + bc.gc * Ai - bc.dc * Ar;
+            ev.template backprop_lineshapes<WEIGHTED>(src, bc, uAr, uAi, uBr, uBi, w, s1, s2);
+          }
+        }
+        release();
+      }
+      T vt[WMC];
+      vt[0] = sw;
+#pragma unroll
+      for (int q = 0; q < NRE; ++q) vt[1 + q] = gre[q];
+#pragma unroll
+      for (int q = 0; q < NIM; ++q) vt[1 + NRE + q] = gim[q];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        vt[1 + NRE + NIM + r] = s1[r];
+        vt[1 + NRE + NIM + NR + r] = s2[r];
+      }
+#pragma unroll
+      for (int q = 0; q < WMC; ++q) {
+        const T s = warp_sum(vt[q]);
+        if (lane == 0) red[warp][q] = double(s);
+      }
+      __syncthreads();
+      for (int v = tid; v < WMC; v += kTile) {
+        double s = 0;
+        for (int w = 0; w < kWarps; ++w) s += red[w][v];
+        colsum[v] = s;
+      }
     }
-#pragma unroll
-    for (int q = 0; q < WMC; ++q) {
-      const T s = warp_sum(vt[q]);
-      if (lane == 0) red[warp][q] = double(s);
-    }
-    __syncthreads();
-    for (int v = tid; v < WMC; v += blockDim.x) {
-      double s = 0;
-      for (int w = 0; w < kTile / 32; ++w) s += red[w][v];
-      colsum[v] = s;
-    }
-    __syncthreads();
+    if (trace && tid == 0) trace[3] = global_ns();
   }
-  if (trace && tid == 0) trace[3] = global_ns();
-  if (timed_out) {
-    // let copies still in flight land before the block exits
-    if (tid == 0) {
-      atomicOr(a.err, 1);
-      for (int64_t q = k; q < my_items && q < k + 2; ++q)
-        mbar_wait_bounded(&bars[q & 1], uint32_t((q >> 1) & 1), kWaitNs);
-    }
-    __syncthreads();
+  const int block_timed_out = __syncthreads_or(timed_out);
+  if (block_timed_out && tid == 0) {
+    // copies no warp waited for (the last one of each stage) land before
+    // shared memory is reused or released
+    const int64_t n_is = s_issued;
+    for (int64_t q = n_is > NST ? n_is - NST : 0; q < n_is; ++q)
+      mbar_wait_bounded(&full_bar[q % NST], uint32_t((q / NST) & 1), kWaitNs);
   }
 
   // ---- block partials (column-major, [W][ld]), then the last block reduces
   float2* part = static_cast<float2*>(a.part);
-  for (int v = tid; v < LY::W; v += blockDim.x)
-    part[size_t(v) * a.ld + blockIdx.x] = (FULL || v >= WMC) ? to_df(colsum[v]) : make_float2(0.f, 0.f);
+  for (int v = FULL ? tid : WMC + tid; v < LY::W; v += blockDim.x) part[size_t(v) * a.ld + b] = to_df(colsum[v]);
   __threadfence();
   __syncthreads();
   if (trace && tid == 0) trace[4] = global_ns();
-  if (tid == 0) is_last = atomicAdd(a.counter, 1u) == unsigned(G - 1);
+  if (tid == 0) {
+    const unsigned old = atomicAdd(a.counter, block_timed_out ? 0x10001u : 1u);
+    s_last = (old & 0xffffu) == unsigned(G - 1);
+    s_timeout = (old >> 16) + (block_timed_out ? 1u : 0u);
+  }
   __syncthreads();
-  if (!is_last) {
+  if (!s_last) {
     if (trace && tid == 0) trace[5] = trace[6] = trace[7] = trace[4];
     return;
   }
   __threadfence();
   {
     // The partial array (column-major, [W][ld] double-float pairs) is brought
-    // into shared memory (the now idle tile stages) by one bulk copy, then
-    // warps 0-6 sum it, two threads per column, double-float (TwoSum)
-    // accumulation, halves combined by one shuffle.  Warp 7 meanwhile derives
-    // the parameter-only gradient constants.
+    // into shared memory (the now idle stage ring) by one bulk copy, then
+    // warps 0-7 sum it, two threads per column, double-float (TwoSum)
+    // accumulation, halves combined by one shuffle.
     const int c0 = FULL ? 0 : WMC;
     const int ncol = LY::W - c0;
     float2* sp = reinterpret_cast<float2*>(smem_raw);
     if (tid == 0) {
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-      mbar_init(&bars[2], 1);
-      mbar_fence_init();
+      asm volatile("fence.proxy.async;" ::: "memory");
       const uint32_t bytes = uint32_t(ncol) * uint32_t(a.ld) * 8u;
-      mbar_arrive_expect_tx(&bars[2], bytes);
-      bulk_g2s(sp, part + size_t(c0) * a.ld, bytes, &bars[2]);
+      mbar_arrive_expect_tx(&part_bar, bytes);
+      bulk_g2s(sp, part + size_t(c0) * a.ld, bytes, &part_bar);
     }
-    __syncthreads();
-    const bool ok = mbar_wait_bounded(&bars[2], 0, kWaitNs);
-    if (__syncthreads_or(!ok) && tid == 0) atomicOr(a.err, 1);
-    if (tid < 224) {
-      // every lane of warps 0-6 runs the same number of iterations, so the
-      // full-warp shuffle below is reached by all of them
+    const bool ok = mbar_wait_bounded(&part_bar, 0, kWaitNs);
+    if (__syncthreads_or(!ok) && tid == 0) s_timeout += 1u;
+    {
+      // every lane runs the same number of iterations, so the full-warp
+      // shuffle below is reached by all of them
       const int half_rows = (G + 1) / 2;
-      for (int e0 = 0; e0 < 2 * ncol; e0 += 224) {
+      for (int e0 = 0; e0 < 2 * ncol; e0 += kTile) {
         const int e = e0 + tid;
         const bool act = e < 2 * ncol;
         const int c = e / 2, h = e & 1;
@@ -754,21 +800,15 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(EvalArgs a, const int* __rest
           colsum[c0 + c] = double(t) + (double(er) + double(eo) + double(err));
         }
       }
-    } else if (GRAD && FULL) {
-      for (int r = tid - 224; r < NR; r += 32)
-        kappa_derivatives(a.dm, r, cc.m0[r], cc.g0[r], cc.kappa[r], cc);
     }
     __syncthreads();
-    for (int v = tid; v < WMC; v += blockDim.x) {
-      if (FULL) a.gram_store[v] = colsum[v];
-      else colsum[v] = a.gram_store[v];
-    }
+    if (FULL)
+      for (int v = tid; v < WMC; v += blockDim.x) a.gram_store[v] = colsum[v];
   }
-  __syncthreads();
   if (trace && tid == 0) trace[5] = global_ns();
-  __syncthreads();
   if (tid == 0) *a.counter = 0u;
-  final_epilogue<S>(a, cc, colsum, GRAD, FULL && GRAD, trace);
+  finish_likelihood<S>(a.result, a.out_nll, a.out_grad, a.km.n_chains, a.km.n_params, cc, colsum, colsum + WMC,
+                       double(dd.n), a.sum_t, a.inv_sum_w, GRAD, FULL && GRAD, s_timeout != 0, trace);
   __syncthreads();
   if (trace && tid == 0) trace[7] = global_ns();
 }

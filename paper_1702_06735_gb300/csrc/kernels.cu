@@ -1,8 +1,10 @@
-// Model-independent kernels run once per event load: kinematic precompute,
-// sum of decay times, weight conversion.
+// Model-independent kernels run once per event load: kinematic precompute
+// and the fixed-order sum of the decay times or MC weights.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "device_tables.hpp"
 #include "kernels.hpp"
@@ -14,17 +16,27 @@ namespace tdmix {
 // Kinematic precompute (one thread per event, fp64): invariants s, width
 // factors X(s) = q^(2L+1) F_L(q r)^2 / sqrt(s) and the spin x barrier factor
 // K_{j,o} of every component ordering.  None depends on fit parameters.
+// Written tile-major (the layout of SampleDev): event i is slot i % 256 of
+// tile i / 256; after the planes of a tile come its decay times (data) or
+// weights (weighted MC); the decay times also go to the component-cache tile.
 // ---------------------------------------------------------------------------
 template <bool F32>
-__global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, int64_t pitch,
-                                                    const DevModel* __restrict__ dm, void* s_out,
-                                                    void* x_out, void* k_out) {
+__global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, const DevModel* __restrict__ dm,
+                                                    unsigned char* planes, int64_t tile_bytes, int npl,
+                                                    const double* __restrict__ t, const double* __restrict__ w,
+                                                    unsigned char* cache, int64_t cache_tile_bytes) {
+  using T = typename std::conditional<F32, float, double>::type;
+  constexpr int TE = kTileEvents;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int64_t tile = i / TE;
+  const int e = int(i % TE);
+  T* out = reinterpret_cast<T*>(planes + tile * tile_bytes);
   V4 p[4];
   for (int a = 0; a < 4; ++a)
     p[a] = {__ldg(mom.p[a][0] + i), __ldg(mom.p[a][1] + i), __ldg(mom.p[a][2] + i), __ldg(mom.p[a][3] + i)};
   const int NS = dm->NS, NX = dm->NX, NT = dm->U * dm->NO;
+  const int NSP = F32 ? 2 * NS : NS;
   double sv[kMaxSPlanes];
   for (int sp = 0; sp < NS; ++sp) {
     V4 P = {0, 0, 0, 0};
@@ -34,12 +46,11 @@ __global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, int6
     const double s = dot(P, P);
     sv[sp] = s;
     if (F32) {
-      float hi = float(s);
-      float lo = float(s - double(hi));
-      static_cast<float*>(s_out)[sp * pitch + i] = hi;
-      static_cast<float*>(s_out)[(NS + sp) * pitch + i] = lo;
+      const float hi = float(s);
+      out[sp * TE + e] = hi;
+      out[(NS + sp) * TE + e] = float(s - double(hi));
     } else {
-      static_cast<double*>(s_out)[sp * pitch + i] = s;
+      out[sp * TE + e] = T(s);
     }
   }
   for (int xp = 0; xp < NX; ++xp) {
@@ -52,25 +63,34 @@ __global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, int6
     for (int l = 0; l < L; ++l) qp *= q2;
     const double F = barrier(L, q2 * dm->r_res * dm->r_res);
     const double X = qp * F * F / sqrt(s);
-    if (F32) static_cast<float*>(x_out)[xp * pitch + i] = float(X);
-    else static_cast<double*>(x_out)[xp * pitch + i] = X;
+    out[(NSP + xp) * TE + e] = T(X);
   }
-  for (int t = 0; t < NT; ++t) {
-    const int* pt = dm->term_parts[t];
-    const double K = spin_barrier(dm->term_spin[t], p[pt[0]], p[pt[1]], p[pt[2]], p[pt[3]], dm->r_res,
+  for (int k = 0; k < NT; ++k) {
+    const int* pt = dm->term_parts[k];
+    const double K = spin_barrier(dm->term_spin[k], p[pt[0]], p[pt[1]], p[pt[2]], p[pt[3]], dm->r_res,
                                   dm->r_parent);
-    if (F32) static_cast<float*>(k_out)[t * pitch + i] = float(K);
-    else static_cast<double*>(k_out)[t * pitch + i] = K;
+    out[(NSP + NX + k) * TE + e] = T(K);
+  }
+  unsigned char* extra = planes + tile * tile_bytes + int64_t(npl) * TE * sizeof(T);
+  if (t) {
+    reinterpret_cast<double*>(extra)[e] = t[i];
+    if (cache)
+      reinterpret_cast<double*>(cache + tile * cache_tile_bytes + int64_t(2 * dm->U) * TE * sizeof(T))[e] = t[i];
+  } else if (w) {
+    reinterpret_cast<T*>(extra)[e] = T(w[i]);
   }
 }
 
-void launch_precompute(bool f32, const Momenta& mom, int64_t n, int64_t pitch, const DevModel* dm, void* s_out,
-                       void* x_out, void* k_out, cudaStream_t st) {
+void launch_precompute(bool f32, const Momenta& mom, int64_t n, const DevModel* dm, void* planes, int64_t tile_bytes,
+                       int npl, const double* t, const double* w, void* cache, int64_t cache_tile_bytes,
+                       cudaStream_t st) {
   if (n <= 0) return;
   const int threads = 256;
   const unsigned blocks = unsigned((n + threads - 1) / threads);
-  if (f32) k_precompute<true><<<blocks, threads, 0, st>>>(mom, n, pitch, dm, s_out, x_out, k_out);
-  else k_precompute<false><<<blocks, threads, 0, st>>>(mom, n, pitch, dm, s_out, x_out, k_out);
+  auto* pl = static_cast<unsigned char*>(planes);
+  auto* ca = static_cast<unsigned char*>(cache);
+  if (f32) k_precompute<true><<<blocks, threads, 0, st>>>(mom, n, dm, pl, tile_bytes, npl, t, w, ca, cache_tile_bytes);
+  else k_precompute<false><<<blocks, threads, 0, st>>>(mom, n, dm, pl, tile_bytes, npl, t, w, ca, cache_tile_bytes);
 }
 
 // Fixed-order sum of a vector (one block).
@@ -89,16 +109,6 @@ __global__ void __launch_bounds__(1024) k_sum(const double* __restrict__ v, int6
 
 void launch_sum(const double* v, int64_t n, double* out, cudaStream_t st) {
   k_sum<<<1, 1024, 0, st>>>(v, n, out);
-}
-
-__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = float(in[i]);
-}
-
-void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t st) {
-  if (n <= 0) return;
-  k_to_f32<<<unsigned((n + 255) / 256), 256, 0, st>>>(in, out, n);
 }
 
 }  // namespace tdmix

@@ -13,10 +13,13 @@ struct Momenta {
   const double* p[4][4];  // [particle][E, px, py, pz], device planes
 };
 
-void launch_precompute(bool f32, const Momenta& mom, int64_t n, int64_t pitch, const DevModel* dm, void* s_out,
-                       void* x_out, void* k_out, cudaStream_t st);
+// Kinematic precompute into the tile-major planes of a sample (see
+// SampleDev); t (data) and w (weighted MC) are device f64 arrays or null;
+// cache (data) receives the decay times of its tiles, or null.
+void launch_precompute(bool f32, const Momenta& mom, int64_t n, const DevModel* dm, void* planes, int64_t tile_bytes,
+                       int npl, const double* t, const double* w, void* cache, int64_t cache_tile_bytes,
+                       cudaStream_t st);
 void launch_sum(const double* v, int64_t n, double* out, cudaStream_t st);
-void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t st);
 
 // Launcher of the model-specialised evaluation kernel.
 struct ShapeOps {
@@ -26,7 +29,9 @@ struct ShapeOps {
   int data_width;  // data columns
   // full: recompute components and run the MC tiles; otherwise read the
   // component cache and reuse the stored MC totals.
-  cudaError_t (*eval)(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a, const int* floating);
+  int n_planes;    // event planes per tile (NPL)
+  int64_t data_tile_bytes, mc_tile_bytes, mc_tile_bytes_weighted, cache_tile_bytes;
+  cudaError_t (*eval)(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a);
   // batched evaluation of serving requests (see serve.cuh)
   cudaError_t (*serve)(bool grad, int grid, cudaStream_t st, const ServeArgs& a);
 };

@@ -31,14 +31,13 @@ cudaStream_t stream_of(tdmix_ctx* ctx);
 int num_sms_of(tdmix_ctx* ctx);
 const CompiledModel& model_of(tdmix_ctx* ctx);
 const ShapeOps* ops_of(tdmix_ctx* ctx);
-const DevModel* dev_model_of(tdmix_ctx* ctx);
-const int* dev_floating_of(tdmix_ctx* ctx);
+const ModelConst& model_const_of(tdmix_ctx* ctx);
 bool is_f32(tdmix_ctx* ctx);
 double inv_sum_w_of(tdmix_ctx* ctx);
 const double* gram_store_of(tdmix_ctx* ctx);
 std::string& error_of(tdmix_ctx* ctx);
-int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* params, void** cache, double** t,
-                         int64_t* pitch, double* sum_t);
+int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* params, void** cache,
+                         int64_t* tile_bytes, double* sum_t);
 int compute_mc_totals(tdmix_ctx* ctx, const double* params, const tdmix_events* one_event);
 }  // namespace internal
 }  // namespace tdmix
@@ -55,9 +54,8 @@ struct SampleRec {
   std::vector<double> planes;  // host copy [16][n] for (re-)admission
   std::vector<double> t;
   bool resident = false;
-  void* cache = nullptr;
-  double* t_dev = nullptr;
-  int64_t pitch = 0;
+  void* cache = nullptr;   // tile-major components and decay times
+  int64_t tile_bytes = 0;
   double sum_t = 0;
   size_t bytes = 0;
   uint64_t last_used = 0;
@@ -138,10 +136,7 @@ int sfail(tdmix_server* s, int code, const std::string& m) {
 int admit(tdmix_server* s, int id) {
   SampleRec& rec = s->samples[id];
   if (rec.resident) return TDMIX_OK;
-  const CompiledModel& m = internal::model_of(s->ctx);
-  const int64_t pitch = (rec.n + 255) / 256 * 256;
-  const size_t es = internal::is_f32(s->ctx) ? 4 : 8;
-  const size_t need = size_t(pitch) * (2 * m.U * es + 8);
+  const size_t need = size_t((rec.n + kTileEvents - 1) / kTileEvents) * internal::ops_of(s->ctx)->cache_tile_bytes;
   while (s->resident_bytes + need > s->budget) {
     int victim = -1;
     uint64_t oldest = UINT64_MAX;
@@ -153,9 +148,7 @@ int admit(tdmix_server* s, int id) {
     if (victim < 0) return TDMIX_ERR_NOMEM;
     SampleRec& v = s->samples[victim];
     cudaFree(v.cache);
-    cudaFree(v.t_dev);
     v.cache = nullptr;
-    v.t_dev = nullptr;
     v.resident = false;
     s->resident_bytes -= v.bytes;
   }
@@ -165,7 +158,7 @@ int admit(tdmix_server* s, int id) {
     for (int c = 0; c < 4; ++c) ev.p[a][c] = rec.planes.data() + size_t(a * 4 + c) * rec.n;
   ev.t = rec.t.data();
   ev.on_device = 0;
-  int rc = internal::take_component_cache(s->ctx, &ev, s->defaults.data(), &rec.cache, &rec.t_dev, &rec.pitch,
+  int rc = internal::take_component_cache(s->ctx, &ev, s->defaults.data(), &rec.cache, &rec.tile_bytes,
                                           &rec.sum_t);
   if (rc) return sfail(s, rc, "admission: " + internal::error_of(s->ctx));
   rec.bytes = need;
@@ -182,13 +175,12 @@ int run_batch(tdmix_server* s, std::vector<Request>& batch, std::vector<Done>& o
   int chunks = 0;
   for (int r = 0; r < nb; ++r) {
     SampleRec& rec = s->samples[batch[r].sample];
-    const int n_tiles = int((rec.n + 255) / 256);
+    const int n_tiles = int((rec.n + kTileEvents - 1) / kTileEvents);
     const int ct = std::max(1, (n_tiles + kServeMaxChunks - 1) / kServeMaxChunks);
     ServeReq& q = s->h_reqs[r];
     q.cache = rec.cache;
-    q.t = rec.t_dev;
     q.n = rec.n;
-    q.pitch = rec.pitch;
+    q.tile_bytes = rec.tile_bytes;
     q.chunk_begin = chunks;
     q.chunk_tiles = ct;
     q.n_tiles = n_tiles;
@@ -204,8 +196,7 @@ int run_batch(tdmix_server* s, std::vector<Request>& batch, std::vector<Done>& o
   a.n_req = nb;
   a.total_chunks = chunks;
   a.params = s->d_params;
-  a.dm = internal::dev_model_of(s->ctx);
-  a.floating = internal::dev_floating_of(s->ctx);
+  a.km = internal::model_const_of(s->ctx);
   a.mc_cols = s->d_mc_cols;
   a.inv_sum_w = s->inv_sum_w;
   a.part = s->d_part;
@@ -448,7 +439,6 @@ void tdmix_server_destroy(tdmix_server* s) {
   if (s->worker.joinable()) s->worker.join();
   for (auto& kv : s->samples) {
     cudaFree(kv.second.cache);
-    cudaFree(kv.second.t_dev);
   }
   cudaStream_t st = s->ctx ? internal::stream_of(s->ctx) : nullptr;
   cudaFree(s->d_reqs);

@@ -29,7 +29,7 @@ struct ServeLayout {
 };
 
 template <class P, class S, bool GRAD>
-__global__ void __launch_bounds__(kTile, 1) k_serve(ServeArgs a) {
+__global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ ServeArgs a) {
   using T = typename P::T;
   using LY = ServeLayout<P, S>;
   constexpr int U = S::U, NR = S::NR, WD = LY::WD, TE = kTile, ES = int(sizeof(T));
@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(ServeArgs a) {
   __shared__ double colsum[WMC + WD];
   __shared__ int chunk_start[kServeMaxRequests + 1];
   __shared__ unsigned is_last;
+  __shared__ int s_timed_out;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   unsigned char* stage[2] = {smem_raw, smem_raw + LY::stage_bytes};
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(ServeArgs a) {
     mbar_fence_init();
   }
   __syncthreads();
-  const int np = a.dm->n_params, nc = a.dm->n_chains;
+  const int np = a.km.n_params, nc = a.km.n_chains;
   uint32_t uses = 0;  // completed barrier phases (both stages), for parity tracking
   bool failed = false;
 
@@ -70,20 +71,17 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(ServeArgs a) {
     const int t0 = lc * q.chunk_tiles;
     const int t1 = min(t0 + q.chunk_tiles, q.n_tiles);
     const int ntl = t1 - t0;
-    auto issue = [&](int j, uint32_t use) {  // tile t0 + j into stage use & 1
+    auto issue = [&](int j, uint32_t use) {  // tile t0 + j into stage use & 1 (one bulk copy)
       const int st = int(use & 1);
-      const int64_t off = int64_t(t0 + j) * TE;
-      mbar_arrive_expect_tx(&bars[st], uint32_t(2 * U * TE * ES + TE * 8));
-      T* dst = reinterpret_cast<T*>(stage[st]);
-      for (int p = 0; p < 2 * U; ++p)
-        bulk_g2s(dst + p * TE, static_cast<const T*>(q.cache) + p * q.pitch + off, TE * ES, &bars[st]);
-      bulk_g2s(stage[st] + 2 * U * TE * ES, q.t + off, TE * 8, &bars[st]);
+      mbar_arrive_expect_tx(&bars[st], uint32_t(q.tile_bytes));
+      bulk_g2s(stage[st], static_cast<const unsigned char*>(q.cache) + int64_t(t0 + j) * q.tile_bytes,
+               uint32_t(q.tile_bytes), &bars[st]);
     };
     if (tid == 0) {
       issue(0, uses);
       if (ntl > 1) issue(1, uses + 1);
     }
-    derive_constants<T>(a.params + size_t(r) * np, a.dm, a.floating, cc, bc);
+    derive_constants<T, U, NR>(a.params + size_t(r) * np, nullptr, a.km, cc, bc);
     __syncthreads();
 
     double lnb = 0.0;
@@ -225,10 +223,15 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(ServeArgs a) {
       }
       colsum[WMC + v] = double(s) + double(e);
     }
+    if (tid == 0) {
+      // a bounded wait that gave up anywhere in the batch is reported (once)
+      s_timed_out = *static_cast<volatile int*>(a.err);
+      if (s_timed_out) *a.err = 0;
+      a.counters[r] = 0u;
+    }
     __syncthreads();
-    if (tid == 0) a.counters[r] = 0u;
-    finish_likelihood<S>(a.results + size_t(r) * (kResHeader + np), nc, np, cc, colsum, colsum + WMC,
-                         double(q.n), q.sum_t, a.inv_sum_w, GRAD, false, a.err, nullptr);
+    finish_likelihood<S>(a.results + size_t(r) * (kResHeader + np), nullptr, nullptr, nc, np, cc, colsum,
+                         colsum + WMC, double(q.n), q.sum_t, a.inv_sum_w, GRAD, false, s_timed_out, nullptr);
     __syncthreads();
     // the bulk-copy target overlapped the stages: stages restart clean below
   }
