@@ -50,10 +50,11 @@ struct tdmix_ctx {
   double* d_sumt = nullptr;
   unsigned long long* d_trace = nullptr;  // per-block phase stamps of the last evaluation (tracing on)
   int64_t* d_ranges = nullptr;            // per-block MC tile ranges [num_sms + 1]
+  double* d_logtab = nullptr;             // logarithm table of the kernels ({1/F, ln F} pairs)
   int64_t ranges_key[3] = {-1, -1, -1};   // (data tiles, MC tiles, grid) the ranges were made for
   double* h_result = nullptr;      // pinned, mapped: written by the kernel for host callers
   double* d_result_map = nullptr;  // device address of h_result
-  void* d_part = nullptr;         // block partials of the evaluation kernel (float2 [width][num_sms])
+  void* d_part = nullptr;         // block partials of the evaluation kernel (float2 [num_sms][width])
   unsigned* d_counter = nullptr;  // blocks finished (returned to 0 by the kernel)
   Sample data, mc;
   double sum_t = 0;
@@ -164,6 +165,18 @@ ModelConst make_model_const(const CompiledModel& m, const std::vector<int>& floa
   }
   for (int q = 0; q < m.n_params(); ++q) k.floating[q] = floating[q] ? 1 : 0;
   return k;
+}
+
+// Table of the kernels' logarithm: {1/F_j, ln F_j} for F_j = 1 + j/128,
+// j = 0..128, each rounded once from extended precision.
+std::vector<double> make_log_table() {
+  std::vector<double> t(2 * 129);
+  for (int j = 0; j <= 128; ++j) {
+    const long double F = 1.0L + (long double)j / 128.0L;
+    t[2 * j] = double(1.0L / F);
+    t[2 * j + 1] = double(std::log(F));
+  }
+  return t;
 }
 
 // Host-side screening of a parameter vector (host pointer only).
@@ -362,6 +375,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.result = result;
   a.out_nll = out_nll;
   a.out_grad = out_grad;
+  a.logtab = ctx->d_logtab;
   a.sum_t = ctx->sum_t;
   a.inv_sum_w = ctx->inv_sum_w;
   a.trace = ctx->d_trace;
@@ -427,6 +441,7 @@ int num_sms_of(tdmix_ctx* ctx) { return ctx->num_sms; }
 const CompiledModel& model_of(tdmix_ctx* ctx) { return ctx->model; }
 const ShapeOps* ops_of(tdmix_ctx* ctx) { return ctx->ops; }
 const ModelConst& model_const_of(tdmix_ctx* ctx) { return ctx->km; }
+const void* log_table_of(tdmix_ctx* ctx) { return ctx->d_logtab; }
 bool is_f32(tdmix_ctx* ctx) { return ctx->f32; }
 double inv_sum_w_of(tdmix_ctx* ctx) { return ctx->inv_sum_w; }
 const double* gram_store_of(tdmix_ctx* ctx) { return ctx->d_gram; }
@@ -507,9 +522,15 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   TDMIX_CK(cudaMalloc(&ctx->d_result, (kResHeader + np) * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_gram, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes) * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_sumt, sizeof(double)));
-  TDMIX_CK(cudaMalloc(&ctx->d_part, size_t(ctx->num_sms) * (ctx->ops->mc_width + ctx->ops->data_width) * 8));
+  // block partial rows [num_sms][width] (+16 bytes: copied in whole 16-byte units)
+  TDMIX_CK(cudaMalloc(&ctx->d_part, size_t(ctx->num_sms) * (ctx->ops->mc_width + ctx->ops->data_width) * 8 + 16));
   TDMIX_CK(cudaMalloc(&ctx->d_counter, sizeof(unsigned)));
   TDMIX_CK(cudaMalloc(&ctx->d_ranges, (ctx->num_sms + 1) * sizeof(int64_t)));
+  {
+    const std::vector<double> lt = make_log_table();
+    TDMIX_CK(cudaMalloc(&ctx->d_logtab, lt.size() * sizeof(double)));
+    TDMIX_CK(cudaMemcpy(ctx->d_logtab, lt.data(), lt.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   TDMIX_CK(cudaMemset(ctx->d_counter, 0, sizeof(unsigned)));
   TDMIX_CK(cudaHostAlloc(&ctx->h_result, (kResHeader + np) * sizeof(double), cudaHostAllocMapped));
   TDMIX_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->d_result_map), ctx->h_result, 0));
@@ -706,6 +727,7 @@ void tdmix_destroy(tdmix_ctx* ctx) {
   cudaFree(ctx->d_part);
   cudaFree(ctx->d_trace);
   cudaFree(ctx->d_ranges);
+  cudaFree(ctx->d_logtab);
   if (ctx->h_result) cudaFreeHost(ctx->h_result);
   for (int c = 0; c < TDMIX_PROF_CLASSES; ++c)
     for (int ph = 0; ph < 2; ++ph)

@@ -65,8 +65,8 @@ struct EvalArgs {
   ModelConst km;
   const double* params;       // device parameter vector, or null: hp holds it
   double hp[kMaxParams];      // parameter vector by value (host callers)
-  void* part;            // float2 [width][ld] double-float block partials (MC columns, then data columns)
-  int64_t ld;            // leading dimension of part (>= grid)
+  void* part;            // float2 [ld][width] double-float block partial rows (MC columns, then data columns)
+  int64_t ld;            // rows of part (>= grid)
   double* gram_store;    // MC column totals of the last pass that ran the MC tiles
   unsigned* counter;     // blocks finished (low 16 bits) and blocks that timed out
                          // (high bits); returned to 0 by the last block
@@ -78,6 +78,7 @@ struct EvalArgs {
   double inv_sum_w;           // 1 / sum of MC weights (the MC event count when unweighted)
   unsigned long long* trace;  // optional: per block kTracePhases globaltimer stamps (ns)
   const int64_t* mc_ranges;   // [grid + 1]: block b takes MC tiles [mc_ranges[b], mc_ranges[b + 1])
+  const void* logtab;         // logarithm table: double2 {1/F, ln F}, F = 1 + j/128, j = 0..128
 };
 
 // Phases stamped by the evaluation kernel when tracing is on: start,
@@ -117,6 +118,7 @@ struct ServeArgs {
   unsigned* counters;       // [n_req] chunks finished (returned to 0)
   double* results;          // [n_req][kResHeader + n_params]
   int* err;
+  const void* logtab;       // logarithm table (as in EvalArgs)
 };
 
 // Result vector written by the evaluation kernel: [nll, N, n_bad or status, sum ln B, grad...]

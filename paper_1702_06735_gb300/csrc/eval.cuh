@@ -68,15 +68,28 @@ struct BlockConst {
   T cA[kMaxComp][2], cB[kMaxComp][2], cA_lo[kMaxComp][2], cB_lo[kMaxComp][2];
   T alpha, beta, gc, dc;
   double x, y, gamma;
+  float xf, yf, gammaf;                // fp32 copies for the fp32 adjoint
+  unsigned long long tlim[2];          // bit patterns of the decay times below which
+                                       // |x|, |y| Gamma t / 2 <= 0.02 (resp. 0.1)
 };
 
-// cosh, sinh of a and cos, sin of b.  For |a|, |b| <= 0.1 (the mixing
-// arguments y Gamma t / 2, x Gamma t / 2 of every event with t below ~40
-// lifetimes at percent-level x, y) the Maclaurin series truncated after the
-// z^5 term (z = a^2 or b^2) is used: the first omitted term is below 3e-21
-// relative.  Otherwise the CUDA math library is called.
-__device__ __forceinline__ void mixing_trig(double a, double b, double& cha, double& sha, double& cb, double& sb) {
-  if (fabs(a) <= 0.1 && fabs(b) <= 0.1) {
+// cosh, sinh of a and cos, sin of b.  The mixing arguments y Gamma t / 2,
+// x Gamma t / 2 are small: at percent-level x, y, |a|, |b| <= 0.02 holds for
+// decay times below ~6.5 lifetimes (nearly every event); there (tier 0) the
+// Maclaurin series through the z^3 term (z = a^2 or b^2) is used (first
+// omitted term below 7e-19 relative); for |a|, |b| <= 0.1 (tier 1, t below
+// ~40 lifetimes) the series run through z^5 (first omitted term below
+// 3e-21); otherwise (tier 2) the CUDA math library is called.  The caller
+// picks the tier from the decay time (BlockConst::tlim).
+__device__ __forceinline__ void mixing_trig(double a, double b, int tier, double& cha, double& sha, double& cb,
+                                            double& sb) {
+  if (tier == 0) {
+    const double za = a * a, zb = b * b;
+    cha = 1.0 + za * (1.0 / 2 + za * (1.0 / 24 + za * (1.0 / 720)));
+    sha = a * (1.0 + za * (1.0 / 6 + za * (1.0 / 120 + za * (1.0 / 5040))));
+    cb = 1.0 - zb * (1.0 / 2 - zb * (1.0 / 24 - zb * (1.0 / 720)));
+    sb = b * (1.0 - zb * (1.0 / 6 - zb * (1.0 / 120 - zb * (1.0 / 5040))));
+  } else if (tier == 1) {
     const double za = a * a, zb = b * b;
     cha = 1.0 + za * (1.0 / 2 + za * (1.0 / 24 + za * (1.0 / 720 + za * (1.0 / 40320 + za * (1.0 / 3628800)))));
     sha = a * (1.0 + za * (1.0 / 6 + za * (1.0 / 120 + za * (1.0 / 5040 + za * (1.0 / 362880 + za * (1.0 / 39916800))))));
@@ -87,6 +100,34 @@ __device__ __forceinline__ void mixing_trig(double a, double b, double& cha, dou
     sha = sinh(a);
     sincos(b, &sb, &cb);
   }
+}
+
+// Natural logarithm by Tang's table-driven method (P. T. P. Tang, ACM Trans.
+// Math. Softw. 16 (1990) 378): v = 2^e m with m in [1, 2); F = 1 + j/128 is
+// the grid point nearest m, so m - F is exact and r = (m - F) / F has
+// |r| <= 2^-8; then ln v = e ln 2 + ln F + ln(1 + r), the last from its
+// Taylor series through r^6 (first omitted term below 2^-58).  tab[j] holds
+// {1/F, ln F} for j = 0 .. 128, made on the host in extended precision.  About
+// ten double-precision operations against several tens for the library
+// logarithm.  The error is below 2^-52 absolute for |ln v| < 1 and relative
+// above (near v = 1 the terms e ln 2 and ln F cancel, so it is not small
+// relative to ln v there; the likelihood sums logarithms and needs the
+// absolute accuracy).  Positive normal v only (the library function takes
+// the rest).
+constexpr int kLogTable = 129;
+__device__ __forceinline__ double log_table(double v, const double2* tab) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  if (bits - 0x0010000000000000ull >= 0x7FE0000000000000ull) return log(v);  // not positive normal
+  const unsigned long long frac = bits & 0x000FFFFFFFFFFFFFull;
+  const int e = int(bits >> 52) - 1023;
+  const double m = __longlong_as_double(static_cast<long long>(frac | 0x3FF0000000000000ull));
+  const unsigned long long j = (frac + (1ull << 44)) >> 45;  // nearest multiple of 1/128, 0 .. 128
+  const double F = __longlong_as_double(static_cast<long long>(0x3FF0000000000000ull + (j << 45)));  // 1 + j/128
+  const double2 t = tab[int(j)];
+  const double r = (m - F) * t.x;
+  const double p = fma(r, fma(r, fma(r, fma(r, -1.0 / 6, 1.0 / 5), -1.0 / 4), 1.0 / 3), -0.5);
+  const double l1p = fma(r * r, p, r);
+  return fma(double(e), 0.69314718055994530942, t.y + l1p);
 }
 
 // Single-precision version for |a|, |b| <= 0.1 (Maclaurin series through the
@@ -266,5 +307,69 @@ struct EventCore {
     }
   }
 };
+
+// One data event's rate from its amplitudes A, Abar (working precision) and
+// decay time: Eq. (mix) as B = 2 |cosh(w) A - sinh(w) Abar|^2 with
+// w = (y + i x) Gamma t / 2, in double precision.  For a B that is positive
+// and finite, adds ln B to lnb and returns true; with GRAD it also forms the
+// sensitivities of ln B: d ln B = 2 Re(tA dA + tB dAbar) and adds
+// d ln B / dx, d ln B / dy to gx, gy.  d ln B = 2 Re(V dZ), V = Z* / |Z|^2,
+// dZ = cosh(w) dA - sinh(w) dAbar + (sinh(w) A - cosh(w) Abar) dw,
+// dw/dy = Gamma t / 2, dw/dx = i Gamma t / 2.  The sensitivities are formed
+// in the working precision; in fp32, cosh(w), sinh(w) and Z are re-derived
+// in fp32 rather than converted from their fp64 values.  `rate` (optional)
+// receives e^{-Gamma t} B.
+template <class P, bool GRAD>
+__device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, const double2* logtab,
+                                          typename P::T Ar_, typename P::T Ai_, typename P::T Br_,
+                                          typename P::T Bi_, double t_e, double& lnb, double* rate,
+                                          typename P::T& tAr, typename P::T& tAi, typename P::T& tBr,
+                                          typename P::T& tBi, typename P::T& gx, typename P::T& gy) {
+  using T = typename P::T;
+  const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
+  const double gt = bc.gamma * t_e;
+  const unsigned long long tb = static_cast<unsigned long long>(__double_as_longlong(t_e));
+  const int tier = tb <= bc.tlim[0] ? 0 : (tb <= bc.tlim[1] ? 1 : 2);  // t < 0 or NaN: tier 2
+  double cha, sha, cb, sb;
+  mixing_trig(0.5 * bc.y * gt, 0.5 * bc.x * gt, tier, cha, sha, cb, sb);
+  const double chr = cha * cb, chi = sha * sb;  // cosh(w)
+  const double shr = sha * cb, shi = cha * sb;  // sinh(w)
+  const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);
+  const double Zi = chr * Ai + chi * Ar - (shr * Bi + shi * Br);
+  const double B = 2.0 * (Zr * Zr + Zi * Zi);
+  if (rate) *rate = exp(-gt) * B;
+  const unsigned long long bb = static_cast<unsigned long long>(__double_as_longlong(B));
+  if (bb - 1ull >= 0x7FEFFFFFFFFFFFFFull) return false;  // B <= 0, infinite or NaN
+  lnb += log_table(B, logtab);
+  if constexpr (GRAD) {
+    T cr, ci, sr, si, Zrt, Zit, tg;
+    if constexpr (P::kF32) {
+      const float tf = float(t_e);
+      tg = bc.gammaf * tf;
+      float chf, shf, cbf, sbf;
+      mixing_trig_f32(0.5f * bc.yf * tg, 0.5f * bc.xf * tg, chf, shf, cbf, sbf);
+      cr = chf * cbf; ci = shf * sbf; sr = shf * cbf; si = chf * sbf;
+      Zrt = 0; Zit = 0;
+      cmac(Zrt, Zit, cr, ci, Ar_, Ai_);
+      cmac(Zrt, Zit, -sr, -si, Br_, Bi_);
+    } else {
+      cr = chr; ci = chi; sr = shr; si = shi;
+      Zrt = Zr; Zit = Zi;
+      tg = gt;
+    }
+    const T iz = rcp<T>(fma(Zrt, Zrt, Zit * Zit));
+    const T Vr = Zrt * iz, Vi = -Zit * iz;
+    tAr = fma(Vr, cr, -Vi * ci);
+    tAi = fma(Vr, ci, Vi * cr);
+    tBr = -fma(Vr, sr, -Vi * si);
+    tBi = -fma(Vr, si, Vi * sr);
+    T Dr = 0, Di = 0;
+    cmac(Dr, Di, sr, si, Ar_, Ai_);
+    cmac(Dr, Di, -cr, -ci, Br_, Bi_);
+    gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
+    gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
+  }
+  return true;
+}
 
 }  // namespace tdmix

@@ -43,6 +43,7 @@ struct CtaConst {
   double x, y, gamma, tau, alpha, beta, gc, dc, ia, ic;
   int chain_comp[kMaxChains], chain_amp[kMaxChains], floating[kMaxParams];
   int nonfinite, domain;
+  double p[kMaxParams];  // the parameter vector
 };
 
 // d ln kappa / d m0 and d ln kappa / d Gamma0 of resonance r (gradient only):
@@ -73,11 +74,13 @@ __device__ inline void kappa_log_derivatives(const ModelConst& km, int r, double
   }
 }
 
-// The kTile threads of a block in parallel: first the parameter vector
-// (device memory, or the kernel parameters when `dparams` is null) is loaded
-// into shared memory, then thread c places chain c's coefficient, thread
-// 64 + r derives resonance r's constants, threads 96, 97 the mixing weights
-// and, with RES_GRAD, thread 128 + r the log-derivatives of kappa_r.
+// Per-evaluation constants, derived by the kTile threads of a block in
+// parallel.  derive_load brings the parameter vector (device memory, or the
+// kernel parameters when `dparams` is null) and the model tables into shared
+// memory; after a barrier, derive_compute has thread c place chain c's
+// coefficient, thread 64 + r derive resonance r's constants, thread 96 the
+// mixing weights and, with RES_GRAD, thread 128 + r the log-derivatives of
+// kappa_r.
 // m0 Gamma(s) = kappa X(s) with, for a mass-dependent width,
 // kappa = m0^2 Gamma0 / (q0^(2L+1) F_L(q0 r)^2); with
 // lambda = Kallen(m0^2, ma^2, mb^2) = 4 m0^2 q0^2 this is
@@ -85,18 +88,21 @@ __device__ inline void kappa_log_derivatives(const ModelConst& km, int r, double
 // (1, 1 + z, 9 + 3z + z^2), z0 = q0^2 r^2; a constant width has
 // kappa = m0 Gamma0.  Only reciprocal square roots and Newton reciprocals
 // sit on the dependent chains (double precision is slow to issue on this
-// GPU).  Ends without a barrier: the caller synchronises.
-template <class T, int U, int NR, bool RES_GRAD = false>
-__device__ inline void derive_constants(const double* __restrict__ dparams, const double* hp, const ModelConst& km,
-                                        CtaConst& cc, BlockConst<T>& bc) {
-  __shared__ double sp[kMaxParams];
+// GPU).  derive_compute ends without a barrier: the caller synchronises.
+template <class T, int U>
+__device__ inline void derive_load(const double* __restrict__ dparams, const double* hp, const ModelConst& km,
+                                   CtaConst& cc, BlockConst<T>& bc) {
   const int tid = threadIdx.x;
   const int nc = km.n_chains, np = km.n_params;
   for (int k = tid; k < np; k += kTile) {
-    sp[k] = dparams ? dparams[k] : hp[k];
+    cc.p[k] = dparams ? dparams[k] : hp[k];
     cc.floating[k] = km.floating[k];
   }
-  for (int j = tid; j < U; j += kTile) cc.cA[j][0] = cc.cA[j][1] = cc.cB[j][0] = cc.cB[j][1] = 0.0;
+  for (int j = tid; j < U; j += kTile) {  // components without a chain in A (or Abar) keep 0
+    cc.cA[j][0] = cc.cA[j][1] = cc.cB[j][0] = cc.cB[j][1] = 0.0;
+    bc.cA[j][0] = bc.cA[j][1] = bc.cB[j][0] = bc.cB[j][1] = T(0);
+    bc.cA_lo[j][0] = bc.cA_lo[j][1] = bc.cB_lo[j][0] = bc.cB_lo[j][1] = T(0);
+  }
   for (int c = tid; c < nc; c += kTile) {
     cc.chain_comp[c] = km.chain_comp[c];
     cc.chain_amp[c] = km.chain_amp[c];
@@ -106,13 +112,27 @@ __device__ inline void derive_constants(const double* __restrict__ dparams, cons
     cc.gamma = km.gamma;
     cc.tau = km.tau;
   }
-  __syncthreads();
+}
+
+template <class T, int U, int NR, bool RES_GRAD = false>
+__device__ inline void derive_compute(const ModelConst& km, CtaConst& cc, BlockConst<T>& bc) {
+  const int tid = threadIdx.x;
+  const int nc = km.n_chains, np = km.n_params;
+  const double* sp = cc.p;
   for (int k = tid; k < np; k += kTile)
     if (!isfinite(sp[k])) atomicOr(&cc.nonfinite, 1);
-  if (tid < nc) {
-    double(*dst)[2] = cc.chain_amp[tid] == 0 ? cc.cA : cc.cB;
-    dst[cc.chain_comp[tid]][0] = sp[2 * tid];
-    dst[cc.chain_comp[tid]][1] = sp[2 * tid + 1];
+  if (tid < nc) {  // each (amplitude, component) has at most one chain
+    const int j = cc.chain_comp[tid];
+    const bool in_a = cc.chain_amp[tid] == 0;
+    double(*dst)[2] = in_a ? cc.cA : cc.cB;
+    T(*hi)[2] = in_a ? bc.cA : bc.cB;
+    T(*lo)[2] = in_a ? bc.cA_lo : bc.cB_lo;
+    for (int q = 0; q < 2; ++q) {
+      const double v = sp[2 * tid + q];
+      dst[j][q] = v;
+      hi[j][q] = T(v);
+      lo[j][q] = T(v - double(T(v)));
+    }
   }
   if (tid >= 64 && tid < 64 + NR) {
     const int r = tid - 64;
@@ -160,21 +180,15 @@ __device__ inline void derive_constants(const double* __restrict__ dparams, cons
     const int r = tid - 128;
     kappa_log_derivatives(km, r, sp[2 * nc + 2 * r], sp[2 * nc + 2 * r + 1], cc);
   }
-  // mixing weights: 1/(1 - y^2) and 1/(1 + x^2) on two threads
-  if (tid == 96 || tid == 97) {
+  // mixing weights on one thread (two independent reciprocals)
+  if (tid == 96) {
     const double x = sp[2 * nc + 2 * NR], y = sp[2 * nc + 2 * NR + 1];
-    if (tid == 96) {
-      if (!(fabs(y) < 1.0)) atomicOr(&cc.domain, 1);
-      cc.ia = rcp<double>(1.0 - y * y);
-      cc.y = y;
-    } else {
-      cc.ic = rcp<double>(1.0 + x * x);
-      cc.x = x;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const double x = cc.x, y = cc.y, ia = cc.ia, ic = cc.ic;
+    if (!(fabs(y) < 1.0)) atomicOr(&cc.domain, 1);
+    const double ia = rcp<double>(1.0 - y * y), ic = rcp<double>(1.0 + x * x);
+    cc.x = x;
+    cc.y = y;
+    cc.ia = ia;
+    cc.ic = ic;
     cc.alpha = ia + ic;
     cc.beta = (x * x + y * y) * ia * ic;
     cc.gc = y * ia;
@@ -182,18 +196,18 @@ __device__ inline void derive_constants(const double* __restrict__ dparams, cons
     bc.x = x;
     bc.y = y;
     bc.gamma = cc.gamma;
+    bc.xf = float(x);
+    bc.yf = float(y);
+    bc.gammaf = float(cc.gamma);
+    // decay-time limits of the mixing-series tiers: |x|, |y| Gamma t / 2 <= 0.02, 0.1
+    const double mg = fmax(fabs(x), fabs(y)) * cc.gamma;
+    const double ig = mg > 0 ? rcp<double>(mg) : INFINITY;
+    bc.tlim[0] = static_cast<unsigned long long>(__double_as_longlong(0.04 * ig));
+    bc.tlim[1] = static_cast<unsigned long long>(__double_as_longlong(0.2 * ig));
     bc.alpha = T(cc.alpha);
     bc.beta = T(cc.beta);
     bc.gc = T(cc.gc);
     bc.dc = T(cc.dc);
-  }
-  for (int j = tid; j < U; j += kTile) {
-    for (int q = 0; q < 2; ++q) {
-      bc.cA[j][q] = T(cc.cA[j][q]);
-      bc.cB[j][q] = T(cc.cB[j][q]);
-      bc.cA_lo[j][q] = T(cc.cA[j][q] - double(bc.cA[j][q]));
-      bc.cB_lo[j][q] = T(cc.cB[j][q] - double(bc.cB[j][q]));
-    }
   }
 }
 
@@ -244,9 +258,9 @@ struct Layout {
   }
   static constexpr int64_t cache_tile_bytes() { return int64_t(NPL_CACHE) * kTile * sizeof(T) + kTile * 8; }
   // dynamic shared memory: the stage ring, reused by the last block for the
-  // partial array of `ld` blocks
+  // partial rows of up to `ld` blocks (copied in whole 16-byte units)
   static constexpr int smem_bytes(bool full, int ld) {
-    const int st = stages(full) * stage_bytes(full), pa = W * ld * 8;
+    const int st = stages(full) * stage_bytes(full), pa = W * ld * 8 + 16;
     return st > pa ? st : pa;
   }
 };
@@ -260,21 +274,21 @@ struct Layout {
 // gc = y/(1-y^2), dc = x/(1+x^2)); with S_jk = sum_e w_e a_j^* a_k and
 // I = S / sum w: <|A|^2> = cA^H I cA, <|Abar|^2> = cB^H I cB,
 // <A Abar*> = cB^H I cA.   NLL = -sum ln B + Gamma sum t + N_d ln N.
-// Warps 0-3 form the four quadratic forms (one per warp, lanes over (j, k),
-// shuffle sum), warps 4-7 meanwhile the vectors S cA, S cB that the
-// coefficient gradient needs; then the logarithm runs on one thread while
-// the others form the gradient.  Used by the last block of an evaluation and,
-// in serving, by the last chunk of each request (at least 256 threads).
+// All threads form the four quadratic forms (two warps per form, shuffle
+// sums); then warp 0 takes the logarithm while warps 1-7 form S cA, S cB and
+// the gradient behind a barrier of their own.  Used by the last block of an
+// evaluation and, in serving, by the last chunk of each request (256
+// threads).
 template <class S>
 __device__ inline void finish_likelihood(double* res, double* onll, double* og, int nc, int np, const CtaConst& cc,
                                          const double* mcs, const double* ds, double Nd, double sum_t, double inv_sw,
-                                         bool want_grad, bool have_res_grad, int timed_out,
+                                         bool want_grad, bool have_res_grad, int timed_out, const double2* logtab,
                                          unsigned long long* trace) {
   constexpr int U = S::U, NR = S::NR;
   constexpr int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2;
   static_assert(2 * U <= 32, "S cA / S cB use four lanes per (which, j)");
   __shared__ double vv[2][U][2];  // S cA, S cB (unnormalised)
-  __shared__ double sh[4];        // AA, BB, Xr, Xi (unnormalised)
+  __shared__ double sh[8];        // AA, BB, Xr, Xi (unnormalised), two halves each
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int status = timed_out ? -7 : (cc.nonfinite ? -5 : (cc.domain ? -6 : 0));
   if (status != 0) {
@@ -293,22 +307,46 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
     si = j == k ? 0.0 : mcs[1 + NRE + lo * (U - 1) - lo * (lo - 1) / 2 + (hi - lo - 1)];
     if (j > k) si = -si;
   };
-  if (warp < 4) {
-    // warp 0: cA^H S cA, 1: cB^H S cB, 2 / 3: Re / Im cB^H S cA
-    const double(*cl)[2] = warp == 0 ? cc.cA : cc.cB;
-    const double(*cr)[2] = warp == 1 ? cc.cB : cc.cA;
+  {
+    // form f = tid / 64 (0: cA^H S cA, 1: cB^H S cB, 2 / 3: Re / Im cB^H S cA)
+    // over the pairs (j, k) = tid % 64, + 64, ...; two warps per form
+    const int f = tid >> 6;
+    const double(*cl)[2] = f == 0 ? cc.cA : cc.cB;
+    const double(*cr)[2] = f == 1 ? cc.cB : cc.cA;
     double acc = 0;
-    for (int e = lane; e < U * U; e += 32) {
+    for (int e = tid & 63; e < U * U; e += 64) {
       const int j = e / U, k = e % U;
       double sr, si;
       s_at(j, k, sr, si);
       const double vr = sr * cr[k][0] - si * cr[k][1], vi = sr * cr[k][1] + si * cr[k][0];
-      acc += warp == 3 ? cl[j][0] * vi - cl[j][1] * vr : cl[j][0] * vr + cl[j][1] * vi;
+      acc += f == 3 ? cl[j][0] * vi - cl[j][1] * vr : cl[j][0] * vr + cl[j][1] * vi;
     }
     acc = warp_sum(acc);
     if (lane == 0) sh[warp] = acc;
-  } else if (warp < 8 && want_grad) {
-    // (which, j) = pair e / 4, k over residue e % 4; four lanes combined by shuffles
+  }
+  __syncthreads();
+  const double al = cc.alpha, be = cc.beta, gc = cc.gc, dc = cc.dc, x = cc.x, y = cc.y, gamma = cc.gamma;
+  const double AA = sh[0] + sh[1], BB = sh[2] + sh[3], Xr = sh[4] + sh[5], Xi = sh[6] + sh[7];
+  const double nbar = (al * AA + be * BB - 2.0 * gc * Xr - 2.0 * dc * Xi) * inv_sw;
+  if (warp == 0) {  // the logarithm; warp 0 takes no part in the gradient
+    if (tid == 0) {
+      const double N = nbar * cc.tau;
+      const double sum_lnb = ds[0], nbad = ds[1];
+      double nll = -sum_lnb + gamma * sum_t + Nd * log_table(N, logtab);
+      if (nbad > 0 || !(N > 0)) nll = nan("");
+      res[0] = nll;
+      res[1] = N;
+      res[2] = nbad;
+      res[3] = sum_lnb;
+      if (onll) *onll = nll;
+      if (trace) trace[6] = global_ns();
+    }
+    return;
+  }
+  if (!want_grad) return;
+  if (warp >= 4) {
+    // S cA, S cB: (which, j) = pair e / 4, k over residue e % 4; four lanes
+    // combined by shuffles
     const int e = tid - 128, pr = e >> 2, q = e & 3;
     const int which = pr / U, j = pr % U;
     double re = 0, im = 0;
@@ -330,23 +368,7 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
       vv[which][j][1] = im;
     }
   }
-  __syncthreads();
-  const double al = cc.alpha, be = cc.beta, gc = cc.gc, dc = cc.dc, x = cc.x, y = cc.y, gamma = cc.gamma;
-  const double AA = sh[0], BB = sh[1], Xr = sh[2], Xi = sh[3];
-  const double nbar = (al * AA + be * BB - 2.0 * gc * Xr - 2.0 * dc * Xi) * inv_sw;
-  if (tid == 0) {
-    const double N = nbar * cc.tau;
-    const double sum_lnb = ds[0], nbad = ds[1];
-    double nll = -sum_lnb + gamma * sum_t + Nd * log(N);
-    if (nbad > 0 || !(N > 0)) nll = nan("");
-    res[0] = nll;
-    res[1] = N;
-    res[2] = nbad;
-    res[3] = sum_lnb;
-    if (onll) *onll = nll;
-    if (trace) trace[6] = global_ns();
-  }
-  if (!want_grad) return;
+  asm volatile("bar.sync 2, 224;" ::: "memory");  // warps 1-7
   auto put = [&](int k, double v) {
     res[kResHeader + k] = v;
     if (og) og[k] = v;
@@ -354,8 +376,6 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
   // d(N_d ln N) = N_d dnbar / nbar, applied to unnormalised sensitivities
   // data columns: [sum ln B, n_bad, d/dx, d/dy, Re gA, Im gA, Re gB, Im gB, s1, s2]
   // chains on threads 32.., resonances on threads 160.., x and y on thread 224
-  // (thread 0 is busy with the logarithm)
-  if (tid < 32) return;
   const double sc = Nd * rcp<double>(nbar) * inv_sw;
   if (tid - 32 < nc) {  // nc <= 64: threads 32 .. 95
     const int ch = tid - 32;
@@ -419,7 +439,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   constexpr int STB = LY::stage_bytes(FULL);
   constexpr int TE = kTile;
   constexpr int ES = int(sizeof(T));
-  static_assert(NR <= 32 && kMaxChains <= 64, "thread roles of derive_constants");
+  static_assert(NR <= 32 && kMaxChains <= 64, "thread roles of derive_compute");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[NST], part_bar;
   __shared__ unsigned released[NST];  // warps done with the stage's current tile
@@ -429,6 +449,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   __shared__ double red[kWarps][WMC > WD ? WMC : WD];
   __shared__ double colsum[LY::W];
   __shared__ unsigned s_last, s_timeout;
+  __shared__ double2 logtab[kLogTable];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
@@ -476,13 +497,20 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
     }
     mbar_init(&part_bar, 1);
     mbar_fence_init();
-    const int64_t first = my_items < NST ? my_items : NST;
-    for (int64_t k = 0; k < first; ++k) issue(k);
-    s_issued = unsigned(first);
+    if (my_items > 0) issue(0);  // the first tile does not depend on the parameters
   }
   if (!FULL)  // stored MC totals of the fixed lineshapes
     for (int v = tid; v < WMC; v += kTile) colsum[v] = a.gram_store[v];
-  derive_constants<T, U, NR, GRAD && FULL>(a.params, a.hp, a.km, cc, bc);
+  for (int j = tid; j < kLogTable; j += kTile) logtab[j] = static_cast<const double2*>(a.logtab)[j];
+  // the parameter loads go out before the other tile copies flood the memory system
+  derive_load<T, U>(a.params, a.hp, a.km, cc, bc);
+  __syncthreads();
+  if (tid == 0) {
+    const int64_t first = my_items < NST ? my_items : NST;
+    for (int64_t k = 1; k < first; ++k) issue(k);
+    s_issued = unsigned(first);
+  }
+  derive_compute<T, U, NR, GRAD && FULL>(a.km, cc, bc);
   __syncthreads();
   if (trace && tid == 0) trace[1] = global_ns();
 
@@ -555,49 +583,10 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
           }
           T Ar_, Ai_, Br_, Bi_;
           ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
-          // Eq. (mix) as 2 |cosh(w) A - sinh(w) Abar|^2, w = (y + i x) Gamma t / 2, in double.
-          const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
-          const double gt = bc.gamma * t_e;
-          double cha, sha, cb, sb;
-          mixing_trig(0.5 * bc.y * gt, 0.5 * bc.x * gt, cha, sha, cb, sb);
-          const double chr = cha * cb, chi = sha * sb;  // cosh(w)
-          const double shr = sha * cb, shi = cha * sb;  // sinh(w)
-          const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);
-          const double Zi = chr * Ai + chi * Ar - (shr * Bi + shi * Br);
-          const double z2 = Zr * Zr + Zi * Zi;
-          const double B = 2.0 * z2;
-          if (a.rates) a.rates[i] = exp(-gt) * B;
-          if (B > 0.0 && B < INFINITY) {
-            lnb += log(B);
+          T tAr, tAi, tBr, tBi;
+          if (mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, t_e, lnb, a.rates ? a.rates + i : nullptr, tAr, tAi,
+                                 tBr, tBi, gx, gy)) {
             if constexpr (GRAD) {
-              // d ln B = 2 Re(V dZ), V = Z* / |Z|^2; dZ = cosh(w) dA - sinh(w) dAbar
-              // + (sinh(w) A - cosh(w) Abar) dw; dw/dy = Gamma t / 2, dw/dx = i Gamma t / 2.
-              // The sensitivities are formed in the working precision; in fp32
-              // cosh(w), sinh(w) and Z are re-derived in fp32 rather than
-              // converted from their fp64 values.
-              T cr, ci, sr, si, Zrt, Zit;
-              if constexpr (P::kF32) {
-                const float gtf = float(bc.gamma) * float(t_e);
-                float chf, shf, cbf, sbf;
-                mixing_trig_f32(0.5f * float(bc.y) * gtf, 0.5f * float(bc.x) * gtf, chf, shf, cbf, sbf);
-                cr = chf * cbf; ci = shf * sbf; sr = shf * cbf; si = chf * sbf;
-                Zrt = 0; Zit = 0;
-                cmac(Zrt, Zit, cr, ci, Ar_, Ai_);
-                cmac(Zrt, Zit, -sr, -si, Br_, Bi_);
-              } else {
-                cr = chr; ci = chi; sr = shr; si = shi;
-                Zrt = Zr; Zit = Zi;
-              }
-              const T iz = rcp<T>(fma(Zrt, Zrt, Zit * Zit));
-              const T Vr = Zrt * iz, Vi = -Zit * iz;
-              const T tAr = fma(Vr, cr, -Vi * ci), tAi = fma(Vr, ci, Vi * cr);
-              const T tBr = -fma(Vr, sr, -Vi * si), tBi = -fma(Vr, si, Vi * sr);
-              T Dr = 0, Di = 0;
-              cmac(Dr, Di, sr, si, Ar_, Ai_);
-              cmac(Dr, Di, -cr, -ci, Br_, Bi_);
-              const T tg = P::kF32 ? T(float(bc.gamma) * float(t_e)) : T(gt);
-              gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
-              gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
 #pragma unroll
               for (int j = 0; j < U; ++j) {
                 cmac(gAr[j], gAi[j], tAr, tAi, ev.ar[j], ev.ai[j]);
@@ -740,75 +729,78 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       mbar_wait_bounded(&full_bar[q % NST], uint32_t((q / NST) & 1), kWaitNs);
   }
 
-  // ---- block partials (column-major, [W][ld]), then the last block reduces
+  // ---- block partials (row b of [G][W]), then the last block reduces
   float2* part = static_cast<float2*>(a.part);
-  for (int v = FULL ? tid : WMC + tid; v < LY::W; v += blockDim.x) part[size_t(v) * a.ld + b] = to_df(colsum[v]);
-  __threadfence();
+  for (int v = FULL ? tid : WMC + tid; v < LY::W; v += blockDim.x) part[size_t(b) * LY::W + v] = to_df(colsum[v]);
   __syncthreads();
   if (trace && tid == 0) trace[4] = global_ns();
   if (tid == 0) {
+    // the barrier orders every thread's partial stores before this release;
+    // the last block's acquire then sees all blocks' partials
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     const unsigned old = atomicAdd(a.counter, block_timed_out ? 0x10001u : 1u);
     s_last = (old & 0xffffu) == unsigned(G - 1);
     s_timeout = (old >> 16) + (block_timed_out ? 1u : 0u);
+    if (s_last) asm volatile("fence.acq_rel.gpu;" ::: "memory");
   }
   __syncthreads();
   if (!s_last) {
     if (trace && tid == 0) trace[5] = trace[6] = trace[7] = trace[4];
     return;
   }
-  __threadfence();
   {
-    // The partial array (column-major, [W][ld] double-float pairs) is brought
-    // into shared memory (the now idle stage ring) by one bulk copy, then
-    // warps 0-7 sum it, two threads per column, double-float (TwoSum)
-    // accumulation, halves combined by one shuffle.
-    const int c0 = FULL ? 0 : WMC;
-    const int ncol = LY::W - c0;
+    // The partial rows of all blocks ([G][W] double-float pairs) come into
+    // shared memory (the idle stage ring) by one bulk copy.  Thread
+    // (column c, half h) sums the rows of its half in order with TwoSum,
+    // lanes on consecutive columns (no bank conflicts); the halves are
+    // combined through shared memory.
+    constexpr int HC = kTile / 2;
+    __shared__ float2 half_sum[HC];
     float2* sp = reinterpret_cast<float2*>(smem_raw);
     if (tid == 0) {
       asm volatile("fence.proxy.async;" ::: "memory");
-      const uint32_t bytes = uint32_t(ncol) * uint32_t(a.ld) * 8u;
+      const uint32_t bytes = (uint32_t(G) * uint32_t(LY::W) * 8u + 15u) & ~15u;
       mbar_arrive_expect_tx(&part_bar, bytes);
-      bulk_g2s(sp, part + size_t(c0) * a.ld, bytes, &part_bar);
+      bulk_g2s(sp, part, bytes, &part_bar);
     }
     const bool ok = mbar_wait_bounded(&part_bar, 0, kWaitNs);
     if (__syncthreads_or(!ok) && tid == 0) s_timeout += 1u;
-    {
-      // every lane runs the same number of iterations, so the full-warp
-      // shuffle below is reached by all of them
-      const int half_rows = (G + 1) / 2;
-      for (int e0 = 0; e0 < 2 * ncol; e0 += kTile) {
-        const int e = e0 + tid;
-        const bool act = e < 2 * ncol;
-        const int c = e / 2, h = e & 1;
-        float s = 0.f, er = 0.f;
-        if (act) {
-          const float2* col = sp + size_t(c) * a.ld;
-          const int r0 = h * half_rows, r1 = h ? G : half_rows;
-          for (int rb = r0; rb < r1; ++rb) {
-            const float2 v = col[rb];
-            float t, err;
-            two_sum(s, v.x, t, err);
-            s = t;
-            er += err + v.y;
-          }
-        }
-        const float so = __shfl_xor_sync(0xffffffffu, s, 1), eo = __shfl_xor_sync(0xffffffffu, er, 1);
-        if (act && h == 0) {
+    const int c0 = FULL ? 0 : WMC;
+    const int ncol = LY::W - c0;
+    const int half_rows = (G + 1) / 2;
+    const int h = tid / HC;
+    for (int cb = 0; cb < ncol; cb += HC) {
+      const int c = cb + tid % HC;
+      float s = 0.f, er = 0.f;
+      if (c < ncol) {
+        const float2* col = sp + c0 + c;
+        const int r0 = h * half_rows, r1 = h ? G : half_rows;
+#pragma unroll 4
+        for (int rb = r0; rb < r1; ++rb) {
+          const float2 v = col[size_t(rb) * LY::W];
           float t, err;
-          two_sum(s, so, t, err);
-          colsum[c0 + c] = double(t) + (double(er) + double(eo) + double(err));
+          two_sum(s, v.x, t, err);
+          s = t;
+          er += err + v.y;
         }
+        if (h == 1) half_sum[c - cb] = make_float2(s, er);
       }
+      __syncthreads();
+      if (h == 0 && c < ncol) {
+        const float2 o = half_sum[c - cb];
+        float t, err;
+        two_sum(s, o.x, t, err);
+        colsum[c0 + c] = double(t) + (double(er) + double(o.y) + double(err));
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (FULL)
       for (int v = tid; v < WMC; v += blockDim.x) a.gram_store[v] = colsum[v];
   }
   if (trace && tid == 0) trace[5] = global_ns();
   if (tid == 0) *a.counter = 0u;
   finish_likelihood<S>(a.result, a.out_nll, a.out_grad, a.km.n_chains, a.km.n_params, cc, colsum, colsum + WMC,
-                       double(dd.n), a.sum_t, a.inv_sum_w, GRAD, FULL && GRAD, s_timeout != 0, trace);
+                       double(dd.n), a.sum_t, a.inv_sum_w, GRAD, FULL && GRAD, s_timeout != 0, logtab, trace);
   __syncthreads();
   if (trace && tid == 0) trace[7] = global_ns();
 }

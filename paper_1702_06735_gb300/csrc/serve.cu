@@ -32,6 +32,7 @@ int num_sms_of(tdmix_ctx* ctx);
 const CompiledModel& model_of(tdmix_ctx* ctx);
 const ShapeOps* ops_of(tdmix_ctx* ctx);
 const ModelConst& model_const_of(tdmix_ctx* ctx);
+const void* log_table_of(tdmix_ctx* ctx);
 bool is_f32(tdmix_ctx* ctx);
 double inv_sum_w_of(tdmix_ctx* ctx);
 const double* gram_store_of(tdmix_ctx* ctx);
@@ -197,6 +198,7 @@ int run_batch(tdmix_server* s, std::vector<Request>& batch, std::vector<Done>& o
   a.total_chunks = chunks;
   a.params = s->d_params;
   a.km = internal::model_const_of(s->ctx);
+  a.logtab = internal::log_table_of(s->ctx);
   a.mc_cols = s->d_mc_cols;
   a.inv_sum_w = s->inv_sum_w;
   a.part = s->d_part;

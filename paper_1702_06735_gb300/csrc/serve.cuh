@@ -43,10 +43,12 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
   __shared__ int chunk_start[kServeMaxRequests + 1];
   __shared__ unsigned is_last;
   __shared__ int s_timed_out;
+  __shared__ double2 logtab[kLogTable];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   unsigned char* stage[2] = {smem_raw, smem_raw + LY::stage_bytes};
   for (int r = tid; r < a.n_req; r += blockDim.x) chunk_start[r] = a.reqs[r].chunk_begin;
+  for (int j = tid; j < kLogTable; j += blockDim.x) logtab[j] = static_cast<const double2*>(a.logtab)[j];
   if (tid == 0) {
     chunk_start[a.n_req] = a.total_chunks;
     mbar_init(&bars[0], 1);
@@ -81,7 +83,9 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       issue(0, uses);
       if (ntl > 1) issue(1, uses + 1);
     }
-    derive_constants<T, U, NR>(a.params + size_t(r) * np, nullptr, a.km, cc, bc);
+    derive_load<T, U>(a.params + size_t(r) * np, nullptr, a.km, cc, bc);
+    __syncthreads();
+    derive_compute<T, U, NR>(a.km, cc, bc);
     __syncthreads();
 
     double lnb = 0.0;
@@ -108,40 +112,9 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
         }
         T Ar_, Ai_, Br_, Bi_;
         ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
-        const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
-        const double gt = bc.gamma * t_e;
-        double cha, sha, cb, sb;
-        mixing_trig(0.5 * bc.y * gt, 0.5 * bc.x * gt, cha, sha, cb, sb);
-        const double chr = cha * cb, chi = sha * sb, shr = sha * cb, shi = cha * sb;
-        const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);
-        const double Zi = chr * Ai + chi * Ar - (shr * Bi + shi * Br);
-        const double B = 2.0 * (Zr * Zr + Zi * Zi);
-        if (B > 0.0 && B < INFINITY) {
-          lnb += log(B);
+        T tAr, tAi, tBr, tBi;
+        if (mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, t_e, lnb, nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
           if constexpr (GRAD) {
-            T cr, ci, sr, si, Zrt, Zit;
-            if constexpr (P::kF32) {
-              const float gtf = float(bc.gamma) * float(t_e);
-              float chf, shf, cbf, sbf;
-              mixing_trig_f32(0.5f * float(bc.y) * gtf, 0.5f * float(bc.x) * gtf, chf, shf, cbf, sbf);
-              cr = chf * cbf; ci = shf * sbf; sr = shf * cbf; si = chf * sbf;
-              Zrt = 0; Zit = 0;
-              cmac(Zrt, Zit, cr, ci, Ar_, Ai_);
-              cmac(Zrt, Zit, -sr, -si, Br_, Bi_);
-            } else {
-              cr = chr; ci = chi; sr = shr; si = shi;
-              Zrt = Zr; Zit = Zi;
-            }
-            const T iz = rcp<T>(fma(Zrt, Zrt, Zit * Zit));
-            const T Vr = Zrt * iz, Vi = -Zit * iz;
-            const T tAr = fma(Vr, cr, -Vi * ci), tAi = fma(Vr, ci, Vi * cr);
-            const T tBr = -fma(Vr, sr, -Vi * si), tBi = -fma(Vr, si, Vi * sr);
-            T Dr = 0, Di = 0;
-            cmac(Dr, Di, sr, si, Ar_, Ai_);
-            cmac(Dr, Di, -cr, -ci, Br_, Bi_);
-            const T tg = P::kF32 ? T(float(bc.gamma) * float(t_e)) : T(gt);
-            gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
-            gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
 #pragma unroll
             for (int k = 0; k < U; ++k) {
               cmac(gAr[k], gAi[k], tAr, tAi, ev.ar[k], ev.ai[k]);
@@ -231,7 +204,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
     }
     __syncthreads();
     finish_likelihood<S>(a.results + size_t(r) * (kResHeader + np), nullptr, nullptr, nc, np, cc, colsum,
-                         colsum + WMC, double(q.n), q.sum_t, a.inv_sum_w, GRAD, false, s_timed_out, nullptr);
+                         colsum + WMC, double(q.n), q.sum_t, a.inv_sum_w, GRAD, false, s_timed_out, logtab, nullptr);
     __syncthreads();
     // the bulk-copy target overlapped the stages: stages restart clean below
   }
