@@ -401,9 +401,18 @@ def run_tdmix(args):
     NS, NX, NT, U = 7, 4, 16, 8
     plane_bytes = NS * 8 + NX * 4 + NT * 4
     bytes_per_launch = N_MC * plane_bytes + N_DATA * (plane_bytes + 8 + 2 * U * 4)
+    # algorithmic fp32 flops (an FMA counts 2) of the full model per event:
+    # MC: lineshapes 162, components 142, Gram 256, A and Abar 128, u 20,
+    # adjoint 534 (W_j 128, terms 252, lineshapes 154); data: lineshapes and
+    # components 304, A and Abar with low parts 256, fp32 Eq. (mix) adjoint 82,
+    # gA/gB 128, adjoint 534 (Eq. (mix) itself is fp64 and not counted)
+    FLOP_MC, FLOP_DATA = 1242, 1304
+    flops_per_launch = N_MC * FLOP_MC + N_DATA * FLOP_DATA
     ev_ms, ev_n = prof32["eval"]
     ev_launch_ms = ev_ms / ev_n
     achieved = bytes_per_launch / (ev_launch_ms * 1e-3) / 1e9
+    alu_tflops = flops_per_launch / (ev_launch_ms * 1e-3) / 1e12
+    ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock (GHz) = 80.5
     peak, peak_kind = measured_peaks()
     launches = sum(n for _, n in prof32.values())
     np_ = len(p0)
@@ -434,7 +443,10 @@ def run_tdmix(args):
         "roofline": {"kernel": "k_eval (one full evaluation, fp32 path)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "launch_ms": ev_launch_ms},
+                     "launch_ms": ev_launch_ms,
+                     "alu": {"achieved": alu_tflops, "peak": ALU_PEAK, "unit": "TFLOP/s", "frac": alu_tflops / ALU_PEAK,
+                             "algorithmic_flops_per_launch": flops_per_launch,
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 8 * np_,
                 "d2h_bytes_per_step": 8 * (4 + np_)},
         "gpu_launches": launches,

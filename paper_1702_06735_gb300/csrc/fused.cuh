@@ -33,7 +33,7 @@ namespace tdmix {
 constexpr int kTile = kTileEvents;
 constexpr int kWarps = kTile / 32;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
-constexpr int kStageBudget = 200 * 1024;     // shared memory for the tile ring
+constexpr int kStageBudget = 192 * 1024;     // shared memory for the tile ring
 
 // Per-evaluation constants in double precision (shared memory of a block).
 struct CtaConst {
@@ -231,6 +231,43 @@ __device__ __forceinline__ V warp_sum(V a) {
   return a;
 }
 
+// Block sum of per-thread values vt[0 .. NQ) into double-float pairs
+// out[q] = (hi, lo), in a fixed order: shuffle trees inside each warp, then
+// the warp sums in warp order.  fp32: everything on the FP32 pipe (TwoSum
+// across warps); converting each warp sum to double would cost a whole warp
+// instruction on the slow fp64 pipe per value, even for one active lane.
+// fp64: double shuffle trees and sums, rounded to a pair at the end.
+// `red` is shared scratch of kWarps x NQ values; ends with a barrier.
+template <class T, int NQ>
+__device__ inline void block_sum_df(const T (&vt)[NQ], T* red, float2* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const T s = warp_sum(vt[q]);
+    if (lane == 0) red[warp * NQ + q] = s;
+  }
+  __syncthreads();
+  for (int q = tid; q < NQ; q += blockDim.x) {
+    if constexpr (sizeof(T) == 4) {
+      float s = 0.f, e = 0.f;
+      for (int w = 0; w < kTile / 32; ++w) {
+        float t, err;
+        two_sum(s, red[w * NQ + q], t, err);
+        s = t;
+        e += err;
+      }
+      float t, err;  // renormalise (hi, lo)
+      two_sum(s, e, t, err);
+      out[q] = make_float2(t, err);
+    } else {
+      double s = 0;
+      for (int w = 0; w < kTile / 32; ++w) s += red[w * NQ + q];
+      out[q] = to_df(s);
+    }
+  }
+  __syncthreads();
+}
+
 template <class P, class S>
 struct Layout {
   using T = typename P::T;
@@ -246,10 +283,11 @@ struct Layout {
   static constexpr int stage_bytes(bool full) {
     return (full ? NPL_FULL : NPL_CACHE) * kTile * int(sizeof(T)) + kTile * 8;
   }
-  // ring depth: as many stages as fit the budget, 2 to 4
+  // ring depth: as many stages as fit the budget, 2 to 6 (the lookahead must
+  // cover the memory latency under full load, a few microseconds)
   static constexpr int stages(bool full) {
     const int n = kStageBudget / stage_bytes(full);
-    return n < 2 ? 2 : (n > 4 ? 4 : n);
+    return n < 2 ? 2 : (n > 6 ? 6 : n);
   }
   // bytes of one tile in global memory (SampleDev::tile_bytes / cache_tile_bytes)
   static constexpr int64_t data_tile_bytes() { return int64_t(NPL_FULL) * kTile * sizeof(T) + kTile * 8; }
@@ -274,11 +312,14 @@ struct Layout {
 // gc = y/(1-y^2), dc = x/(1+x^2)); with S_jk = sum_e w_e a_j^* a_k and
 // I = S / sum w: <|A|^2> = cA^H I cA, <|Abar|^2> = cB^H I cB,
 // <A Abar*> = cB^H I cA.   NLL = -sum ln B + Gamma sum t + N_d ln N.
-// All threads form the four quadratic forms (two warps per form, shuffle
-// sums); then warp 0 takes the logarithm while warps 1-7 form S cA, S cB and
-// the gradient behind a barrier of their own.  Used by the last block of an
-// evaluation and, in serving, by the last chunk of each request (256
-// threads).
+// The vectors S cA, S cB come first (one product per thread, shuffle sums
+// over k), then the four quadratic forms from them (c^H (S c)): fp64 issue
+// throughput, not latency, bounds this block-wide work on this GPU, and this
+// order needs about a third of the fp64 instructions of forming each
+// quadratic form from S directly.  Warp 0 then takes the logarithm while
+// warps 1-7 form the gradient.  Used by the
+// last block of an evaluation and, in serving, by the last chunk of each
+// request (256 threads).
 template <class S>
 __device__ inline void finish_likelihood(double* res, double* onll, double* og, int nc, int np, const CtaConst& cc,
                                          const double* mcs, const double* ds, double Nd, double sum_t, double inv_sw,
@@ -286,9 +327,9 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
                                          unsigned long long* trace) {
   constexpr int U = S::U, NR = S::NR;
   constexpr int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2;
-  static_assert(2 * U <= 32, "S cA / S cB use four lanes per (which, j)");
+  static_assert(U <= 16, "lane groups of at most 16 over the components");
   __shared__ double vv[2][U][2];  // S cA, S cB (unnormalised)
-  __shared__ double sh[8];        // AA, BB, Xr, Xi (unnormalised), two halves each
+  __shared__ double sh[4];        // AA, BB, Xr, Xi (unnormalised)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int status = timed_out ? -7 : (cc.nonfinite ? -5 : (cc.domain ? -6 : 0));
   if (status != 0) {
@@ -307,26 +348,48 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
     si = j == k ? 0.0 : mcs[1 + NRE + lo * (U - 1) - lo * (lo - 1) / 2 + (hi - lo - 1)];
     if (j > k) si = -si;
   };
-  {
-    // form f = tid / 64 (0: cA^H S cA, 1: cB^H S cB, 2 / 3: Re / Im cB^H S cA)
-    // over the pairs (j, k) = tid % 64, + 64, ...; two warps per form
-    const int f = tid >> 6;
-    const double(*cl)[2] = f == 0 ? cc.cA : cc.cB;
-    const double(*cr)[2] = f == 1 ? cc.cB : cc.cA;
-    double acc = 0;
-    for (int e = tid & 63; e < U * U; e += 64) {
-      const int j = e / U, k = e % U;
+  // (1) v = S c for c = cA (which 0) and cB (which 1): thread = (which, j, k)
+  //     in groups of KG lanes over k, shuffle sums within the group
+  constexpr int KG = U <= 1 ? 1 : (U <= 2 ? 2 : (U <= 4 ? 4 : (U <= 8 ? 8 : 16)));
+  constexpr int PAIRS_PER_PASS = kTile / KG;
+  for (int p0 = 0; p0 < 2 * U; p0 += PAIRS_PER_PASS) {
+    const int pr = p0 + tid / KG, k = tid % KG;
+    const int which = pr / U, j = pr % U;
+    double re = 0, im = 0;
+    if (pr < 2 * U && k < U) {
+      const double(*c)[2] = which ? cc.cB : cc.cA;
       double sr, si;
       s_at(j, k, sr, si);
-      const double vr = sr * cr[k][0] - si * cr[k][1], vi = sr * cr[k][1] + si * cr[k][0];
-      acc += f == 3 ? cl[j][0] * vi - cl[j][1] * vr : cl[j][0] * vr + cl[j][1] * vi;
+      re = sr * c[k][0] - si * c[k][1];
+      im = sr * c[k][1] + si * c[k][0];
     }
-    acc = warp_sum(acc);
-    if (lane == 0) sh[warp] = acc;
+#pragma unroll
+    for (int off = 1; off < KG; off <<= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, off);
+      im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    if (pr < 2 * U && k == 0) {
+      vv[which][j][0] = re;
+      vv[which][j][1] = im;
+    }
+  }
+  __syncthreads();
+  // (2) the four forms from v: f = 0: cA^H vA, 1: cB^H vB, 2 / 3: Re / Im cB^H vA
+  if (tid < (4 * KG + 31) / 32 * 32) {  // whole warps, for the shuffles
+    const int f = tid / KG, j = tid % KG;
+    double acc = 0;
+    if (f < 4 && j < U) {
+      const double(*cl)[2] = f == 0 ? cc.cA : cc.cB;
+      const double* v = vv[f == 1 ? 1 : 0][j];
+      acc = f == 3 ? cl[j][0] * v[1] - cl[j][1] * v[0] : cl[j][0] * v[0] + cl[j][1] * v[1];
+    }
+#pragma unroll
+    for (int off = 1; off < KG; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (f < 4 && j == 0) sh[f] = acc;
   }
   __syncthreads();
   const double al = cc.alpha, be = cc.beta, gc = cc.gc, dc = cc.dc, x = cc.x, y = cc.y, gamma = cc.gamma;
-  const double AA = sh[0] + sh[1], BB = sh[2] + sh[3], Xr = sh[4] + sh[5], Xi = sh[6] + sh[7];
+  const double AA = sh[0], BB = sh[1], Xr = sh[2], Xi = sh[3];
   const double nbar = (al * AA + be * BB - 2.0 * gc * Xr - 2.0 * dc * Xi) * inv_sw;
   if (warp == 0) {  // the logarithm; warp 0 takes no part in the gradient
     if (tid == 0) {
@@ -344,31 +407,6 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
     return;
   }
   if (!want_grad) return;
-  if (warp >= 4) {
-    // S cA, S cB: (which, j) = pair e / 4, k over residue e % 4; four lanes
-    // combined by shuffles
-    const int e = tid - 128, pr = e >> 2, q = e & 3;
-    const int which = pr / U, j = pr % U;
-    double re = 0, im = 0;
-    if (pr < 2 * U) {
-      const double(*c)[2] = which ? cc.cB : cc.cA;
-      for (int k = q; k < U; k += 4) {
-        double sr, si;
-        s_at(j, k, sr, si);
-        re += sr * c[k][0] - si * c[k][1];
-        im += sr * c[k][1] + si * c[k][0];
-      }
-    }
-    re += __shfl_xor_sync(0xffffffffu, re, 1);
-    im += __shfl_xor_sync(0xffffffffu, im, 1);
-    re += __shfl_xor_sync(0xffffffffu, re, 2);
-    im += __shfl_xor_sync(0xffffffffu, im, 2);
-    if (pr < 2 * U && q == 0) {
-      vv[which][j][0] = re;
-      vv[which][j][1] = im;
-    }
-  }
-  asm volatile("bar.sync 2, 224;" ::: "memory");  // warps 1-7
   auto put = [&](int k, double v) {
     res[kResHeader + k] = v;
     if (og) og[k] = v;
@@ -446,7 +484,9 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   __shared__ unsigned s_issued;       // items whose copy has been issued
   __shared__ CtaConst cc;
   __shared__ BlockConst<T> bc;
-  __shared__ double red[kWarps][WMC > WD ? WMC : WD];
+  __shared__ T red[kWarps * (WMC > WD ? WMC : WD)];
+  __shared__ double red_lnb[kWarps];
+  __shared__ float2 rowp[LY::W];   // this block's partial row (double-float)
   __shared__ double colsum[LY::W];
   __shared__ unsigned s_last, s_timeout;
   __shared__ double2 logtab[kLogTable];
@@ -600,41 +640,42 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
         }
         release();
       }
-      // block sum of the data accumulators -> colsum[WMC ..]
+      // block sums of the data accumulators -> rowp[WMC ..]
       {
-        const double v0 = warp_sum(lnb), v1 = warp_sum(double(bad));
+        __shared__ int red_bad[kWarps];
+        const double v0 = warp_sum(lnb);
+        const int v1 = warp_sum(bad);
         if (lane == 0) {
-          red[warp][0] = v0;
-          red[warp][1] = v1;
+          red_lnb[warp] = v0;
+          red_bad[warp] = v1;
+        }
+        T vt[WD - 2];
+        vt[0] = gx;
+        vt[1] = gy;
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          vt[2 + j] = gAr[j];
+          vt[2 + U + j] = gAi[j];
+          vt[2 + 2 * U + j] = gBr[j];
+          vt[2 + 3 * U + j] = gBi[j];
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          vt[2 + 4 * U + r] = s1[r];
+          vt[2 + 4 * U + NR + r] = s2[r];
+        }
+        block_sum_df<T, WD - 2>(vt, red, rowp + WMC + 2);  // ends with a barrier
+        if (tid == 0) {
+          double sl = 0;
+          int sb = 0;
+          for (int w = 0; w < kWarps; ++w) {
+            sl += red_lnb[w];
+            sb += red_bad[w];
+          }
+          rowp[WMC] = to_df(sl);
+          rowp[WMC + 1] = make_float2(float(sb), 0.f);
         }
       }
-      T vt[WD - 2];
-      vt[0] = gx;
-      vt[1] = gy;
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        vt[2 + j] = gAr[j];
-        vt[2 + U + j] = gAi[j];
-        vt[2 + 2 * U + j] = gBr[j];
-        vt[2 + 3 * U + j] = gBi[j];
-      }
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        vt[2 + 4 * U + r] = s1[r];
-        vt[2 + 4 * U + NR + r] = s2[r];
-      }
-#pragma unroll
-      for (int q = 0; q < WD - 2; ++q) {
-        const T s = warp_sum(vt[q]);
-        if (lane == 0) red[warp][2 + q] = double(s);
-      }
-      __syncthreads();
-      for (int v = tid; v < WD; v += kTile) {
-        double s = 0;
-        for (int w = 0; w < kWarps; ++w) s += red[w][v];
-        colsum[WMC + v] = s;
-      }
-      __syncthreads();
     }
     if (trace && tid == 0) trace[2] = global_ns();
 
@@ -706,17 +747,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
         vt[1 + NRE + NIM + r] = s1[r];
         vt[1 + NRE + NIM + NR + r] = s2[r];
       }
-#pragma unroll
-      for (int q = 0; q < WMC; ++q) {
-        const T s = warp_sum(vt[q]);
-        if (lane == 0) red[warp][q] = double(s);
-      }
-      __syncthreads();
-      for (int v = tid; v < WMC; v += kTile) {
-        double s = 0;
-        for (int w = 0; w < kWarps; ++w) s += red[w][v];
-        colsum[v] = s;
-      }
+      block_sum_df<T, WMC>(vt, red, rowp);
     }
     if (trace && tid == 0) trace[3] = global_ns();
   }
@@ -731,7 +762,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
 
   // ---- block partials (row b of [G][W]), then the last block reduces
   float2* part = static_cast<float2*>(a.part);
-  for (int v = FULL ? tid : WMC + tid; v < LY::W; v += blockDim.x) part[size_t(b) * LY::W + v] = to_df(colsum[v]);
+  for (int v = FULL ? tid : WMC + tid; v < LY::W; v += blockDim.x) part[size_t(b) * LY::W + v] = rowp[v];
   __syncthreads();
   if (trace && tid == 0) trace[4] = global_ns();
   if (tid == 0) {
@@ -773,15 +804,38 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       const int c = cb + tid % HC;
       float s = 0.f, er = 0.f;
       if (c < ncol) {
+        // rows in four interleaved chains (independent loads and adds), then
+        // the chains combined in order
         const float2* col = sp + c0 + c;
         const int r0 = h * half_rows, r1 = h ? G : half_rows;
-#pragma unroll 4
-        for (int rb = r0; rb < r1; ++rb) {
-          const float2 v = col[size_t(rb) * LY::W];
+        float s4[4] = {0.f, 0.f, 0.f, 0.f}, e4[4] = {0.f, 0.f, 0.f, 0.f};
+        int rb = r0;
+        for (; rb + 4 <= r1; rb += 4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = col[size_t(rb + q) * LY::W];
+            float t, err;
+            two_sum(s4[q], v.x, t, err);
+            s4[q] = t;
+            e4[q] += err + v.y;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (rb + q < r1) {
+            const float2 v = col[size_t(rb + q) * LY::W];
+            float t, err;
+            two_sum(s4[q], v.x, t, err);
+            s4[q] = t;
+            e4[q] += err + v.y;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
           float t, err;
-          two_sum(s, v.x, t, err);
+          two_sum(s, s4[q], t, err);
           s = t;
-          er += err + v.y;
+          er += err + e4[q];
         }
         if (h == 1) half_sum[c - cb] = make_float2(s, er);
       }

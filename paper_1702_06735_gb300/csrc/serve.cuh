@@ -38,7 +38,10 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
   __shared__ __align__(8) uint64_t bars[3];
   __shared__ CtaConst cc;
   __shared__ BlockConst<T> bc;
-  __shared__ double red[kTile / 32][WD];
+  __shared__ T red[(kTile / 32) * (2 + 4 * U)];
+  __shared__ double red_lnb[kTile / 32];
+  __shared__ int red_bad[kTile / 32];
+  __shared__ float2 rowp[WD];
   __shared__ double colsum[WMC + WD];
   __shared__ int chunk_start[kServeMaxRequests + 1];
   __shared__ unsigned is_last;
@@ -135,12 +138,13 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       }
       __syncthreads();
     }
-    // chunk partial -> its row
+    // chunk partial -> its row (double-float; see block_sum_df)
     {
-      const double v0 = warp_sum(lnb), v1 = warp_sum(double(bad));
+      const double v0 = warp_sum(lnb);
+      const int v1 = warp_sum(bad);
       if (lane == 0) {
-        red[warp][0] = v0;
-        red[warp][1] = v1;
+        red_lnb[warp] = v0;
+        red_bad[warp] = v1;
       }
       T vt[2 + 4 * U];
       vt[0] = gx;
@@ -152,19 +156,22 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
         vt[2 + 2 * U + k] = gBr[k];
         vt[2 + 3 * U + k] = gBi[k];
       }
-#pragma unroll
-      for (int v = 0; v < 2 + 4 * U; ++v) {
-        const T s = warp_sum(vt[v]);
-        if (lane == 0) red[warp][2 + v] = double(s);
+      block_sum_df<T, 2 + 4 * U>(vt, red, rowp + 2);  // ends with a barrier
+    }
+    float2* part = static_cast<float2*>(a.part);
+    if (tid == 0) {
+      double sl = 0;
+      int sb = 0;
+      for (int w = 0; w < kTile / 32; ++w) {
+        sl += red_lnb[w];
+        sb += red_bad[w];
       }
+      rowp[0] = to_df(sl);
+      rowp[1] = make_float2(float(sb), 0.f);
     }
     __syncthreads();
-    float2* part = static_cast<float2*>(a.part);
-    for (int v = tid; v < WD; v += blockDim.x) {
-      double s = 0;
-      for (int w = 0; w < kTile / 32; ++w) s += red[w][v];
-      part[size_t(c) * WD + v] = v < 4 + 4 * U ? to_df(s) : make_float2(0.f, 0.f);
-    }
+    for (int v = tid; v < WD; v += blockDim.x)
+      part[size_t(c) * WD + v] = v < 4 + 4 * U ? rowp[v] : make_float2(0.f, 0.f);
     __threadfence();
     __syncthreads();
     if (tid == 0) is_last = atomicAdd(a.counters + r, 1u) == unsigned(q.n_chunks - 1);
