@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="tdmix", choices=["tdmix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--toys", type=int, default=32, help="pseudo-experiments in the serving toy study (0: skip)")
+    ap.add_argument("--flush-l2", action="store_true",
+                    help="write 256 MB between timed steps (default: none; the inputs of one evaluation exceed L2)")
     ap.add_argument("--quick", action="store_true",
                     help="profiling runs: flat-phase-space data instead of accept/reject (same sizes, same kernels)")
     return ap.parse_args()
@@ -334,7 +336,8 @@ def run_tdmix(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         t_wall0 = time.perf_counter()
         for k in range(K):
-            flush.zero_()
+            if args.flush_l2:
+                flush.zero_()
             ev[k][0].record(stream)
             c.nll_device(P[W + k], out[W + k:W + k + 1], grad[W + k])
             ev[k][1].record(stream)
@@ -362,12 +365,13 @@ def run_tdmix(args):
     p0 = c32.default_params()
     fl = np.ones(len(p0), dtype=bool)
     fl[[0, 1]] = False
+    host_params = [step_params(p0, fl, 6000 + k) for k in range(args.steps)]  # made before timing
     for k in range(args.warmup):
         c32.nll(step_params(p0, fl, 5000 + k))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        c32.nll(step_params(p0, fl, 6000 + k))
+        c32.nll(host_params[k])
     e2e_s = time.perf_counter() - t0
 
     # the paper's fit benchmark style: fixed model, only x and y float (cached path)
@@ -413,6 +417,7 @@ def run_tdmix(args):
     achieved = bytes_per_launch / (ev_launch_ms * 1e-3) / 1e9
     alu_tflops = flops_per_launch / (ev_launch_ms * 1e-3) / 1e12
     ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock (GHz) = 80.5
+    l2_mb = torch.cuda.get_device_properties(dev).L2_cache_size / 1e6
     peak, peak_kind = measured_peaks()
     launches = sum(n for _, n in prof32.values())
     np_ = len(p0)
@@ -432,7 +437,10 @@ def run_tdmix(args):
         "config": {"workload": f"{MODEL}: 16 chains (8 shared components), 44 floating params, "
                                f"{N_DATA} accept/reject events (x=0.49%, y=0.61%), {N_MC} flat MC events; "
                                f"every parameter moved each step",
-                   "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                   "l2": ("flushed between timed steps (256 MB write, outside the step events)" if args.flush_l2 else
+                          f"not flushed: one evaluation streams {bytes_per_launch / 1e6:.0f} MB of event planes, "
+                          f"more than the {l2_mb:.0f} MB L2, so every step reads its inputs from HBM (ncu DRAM bytes "
+                          f"per launch with warm caches: see profiles/)"),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "fp64_path": {"value": 1000.0 / (sum(ms64) / len(ms64)), "unit": "evals/s",
                       "ms_per_step": sum(ms64) / len(ms64), "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof64.items()}},

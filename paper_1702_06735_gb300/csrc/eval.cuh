@@ -68,6 +68,7 @@ struct BlockConst {
   T cA[kMaxComp][2], cB[kMaxComp][2], cA_lo[kMaxComp][2], cB_lo[kMaxComp][2];
   T alpha, beta, gc, dc;
   double x, y, gamma;
+  double hx, hy;                       // x Gamma / 2, y Gamma / 2
   float xf, yf, gammaf;                // fp32 copies for the fp32 adjoint
   unsigned long long tlim[2];          // bit patterns of the decay times below which
                                        // |x|, |y| Gamma t / 2 <= 0.02 (resp. 0.1)
@@ -331,7 +332,7 @@ __device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, c
   const unsigned long long tb = static_cast<unsigned long long>(__double_as_longlong(t_e));
   const int tier = tb <= bc.tlim[0] ? 0 : (tb <= bc.tlim[1] ? 1 : 2);  // t < 0 or NaN: tier 2
   double cha, sha, cb, sb;
-  mixing_trig(0.5 * bc.y * gt, 0.5 * bc.x * gt, tier, cha, sha, cb, sb);
+  mixing_trig(bc.hy * t_e, bc.hx * t_e, tier, cha, sha, cb, sb);
   const double chr = cha * cb, chi = sha * sb;  // cosh(w)
   const double shr = sha * cb, shi = cha * sb;  // sinh(w)
   const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);

@@ -196,6 +196,8 @@ __device__ inline void derive_compute(const ModelConst& km, CtaConst& cc, BlockC
     bc.x = x;
     bc.y = y;
     bc.gamma = cc.gamma;
+    bc.hx = 0.5 * x * cc.gamma;
+    bc.hy = 0.5 * y * cc.gamma;
     bc.xf = float(x);
     bc.yf = float(y);
     bc.gammaf = float(cc.gamma);
