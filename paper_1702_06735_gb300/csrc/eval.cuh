@@ -58,15 +58,23 @@ __device__ __forceinline__ float rcp<float>(float v) {
   return fmaf(r, e, r);
 }
 
-// Per-block copy of the per-evaluation constants in the working precision.
+// Four values read together (one 128-bit shared load in fp32, two in fp64).
+template <class T>
+struct alignas(4 * sizeof(T)) Quad {
+  T x, y, z, w;
+};
+
+// Per-block copy of the per-evaluation constants in the working precision,
+// grouped by use so that each group is one vector load per event.
 template <class T>
 struct BlockConst {
-  // working-precision values; in fp32 the *_lo parts carry the rounding
+  // working-precision values; in fp32 the lo parts carry the rounding
   // residual of the double-precision constant (value = hi + lo), so that no
   // systematic fp32 rounding enters every event in the same direction
-  T m2[kMaxRes], m2_lo[kMaxRes], kappa[kMaxRes], kappa_lo[kMaxRes];
-  T cA[kMaxComp][2], cB[kMaxComp][2], cA_lo[kMaxComp][2], cB_lo[kMaxComp][2];
-  T alpha, beta, gc, dc;
+  Quad<T> res[kMaxRes];     // resonance r: {m0^2, its lo part, kappa, its lo part}
+  Quad<T> cab[kMaxComp];    // component j: {Re cA, Im cA, Re cB, Im cB}
+  Quad<T> cab_lo[kMaxComp]; // their lo parts
+  Quad<T> mix;              // {alpha, beta, gc, dc}
   double x, y, gamma;
   double hx, hy;                       // x Gamma / 2, y Gamma / 2
   float xf, yf, gammaf;                // fp32 copies for the fp32 adjoint
@@ -191,17 +199,18 @@ struct EventCore {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int r = S::bres(b), sp = S::bs(b), xp = S::bx(b);
+      const Quad<T> R = bc.res[r];
       T delta;
       if constexpr (P::kF32) {
-        delta = (bc.m2[r] - src.s_hi(sp)) + (bc.m2_lo[r] - src.s_lo(sp));
+        delta = (R.x - src.s_hi(sp)) + (R.y - src.s_lo(sp));
       } else {
-        delta = bc.m2[r] - src.s_hi(sp);
+        delta = R.x - src.s_hi(sp);
       }
       T X = T(1);
       if (xp >= 0) X = src.x(xp);
       T im;
-      if constexpr (P::kF32) im = fma(bc.kappa[r], X, bc.kappa_lo[r] * X);
-      else im = bc.kappa[r] * X;
+      if constexpr (P::kF32) im = fma(R.z, X, R.w * X);
+      else im = R.z * X;
       T inv = rcp<T>(fma(delta, delta, im * im));
       bwr[b] = delta * inv;
       bwi[b] = im * inv;
@@ -246,11 +255,13 @@ struct EventCore {
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       if constexpr (LO && P::kF32) {
-        cmac(Ar, Ai, bc.cA_lo[j][0], bc.cA_lo[j][1], ar[j], ai[j]);
-        cmac(Br, Bi, bc.cB_lo[j][0], bc.cB_lo[j][1], ar[j], ai[j]);
+        const Quad<T> L = bc.cab_lo[j];
+        cmac(Ar, Ai, L.x, L.y, ar[j], ai[j]);
+        cmac(Br, Bi, L.z, L.w, ar[j], ai[j]);
       }
-      cmac(Ar, Ai, bc.cA[j][0], bc.cA[j][1], ar[j], ai[j]);
-      cmac(Br, Bi, bc.cB[j][0], bc.cB[j][1], ar[j], ai[j]);
+      const Quad<T> C = bc.cab[j];
+      cmac(Ar, Ai, C.x, C.y, ar[j], ai[j]);
+      cmac(Br, Bi, C.z, C.w, ar[j], ai[j]);
     }
   }
 
@@ -271,8 +282,9 @@ struct EventCore {
       for (int j = 0; j < U; ++j) {
         // W_j = gA cA_j + gB cB_j
         T Wr = 0, Wi = 0;
-        cmac(Wr, Wi, gAr, gAi, bc.cA[j][0], bc.cA[j][1]);
-        cmac(Wr, Wi, gBr, gBi, bc.cB[j][0], bc.cB[j][1]);
+        const Quad<T> C = bc.cab[j];
+        cmac(Wr, Wi, gAr, gAi, C.x, C.y);
+        cmac(Wr, Wi, gBr, gBi, C.z, C.w);
 #pragma unroll
         for (int o = 0; o < NO; ++o) {
           const int t = j * NO + o;

@@ -100,8 +100,8 @@ __device__ inline void derive_load(const double* __restrict__ dparams, const dou
   }
   for (int j = tid; j < U; j += kTile) {  // components without a chain in A (or Abar) keep 0
     cc.cA[j][0] = cc.cA[j][1] = cc.cB[j][0] = cc.cB[j][1] = 0.0;
-    bc.cA[j][0] = bc.cA[j][1] = bc.cB[j][0] = bc.cB[j][1] = T(0);
-    bc.cA_lo[j][0] = bc.cA_lo[j][1] = bc.cB_lo[j][0] = bc.cB_lo[j][1] = T(0);
+    bc.cab[j] = Quad<T>{T(0), T(0), T(0), T(0)};
+    bc.cab_lo[j] = Quad<T>{T(0), T(0), T(0), T(0)};
   }
   for (int c = tid; c < nc; c += kTile) {
     cc.chain_comp[c] = km.chain_comp[c];
@@ -125,13 +125,13 @@ __device__ inline void derive_compute(const ModelConst& km, CtaConst& cc, BlockC
     const int j = cc.chain_comp[tid];
     const bool in_a = cc.chain_amp[tid] == 0;
     double(*dst)[2] = in_a ? cc.cA : cc.cB;
-    T(*hi)[2] = in_a ? bc.cA : bc.cB;
-    T(*lo)[2] = in_a ? bc.cA_lo : bc.cB_lo;
+    T* hi = in_a ? &bc.cab[j].x : &bc.cab[j].z;  // (re, im) adjacent
+    T* lo = in_a ? &bc.cab_lo[j].x : &bc.cab_lo[j].z;
     for (int q = 0; q < 2; ++q) {
       const double v = sp[2 * tid + q];
       dst[j][q] = v;
-      hi[j][q] = T(v);
-      lo[j][q] = T(v - double(T(v)));
+      hi[q] = T(v);
+      lo[q] = T(v - double(T(v)));
     }
   }
   if (tid >= 64 && tid < 64 + NR) {
@@ -165,16 +165,18 @@ __device__ inline void derive_compute(const ModelConst& km, CtaConst& cc, BlockC
     cc.g0[r] = g0;
     cc.m2[r] = u;
     cc.kappa[r] = kap;
+    Quad<T> R;
     if constexpr (sizeof(T) == 4) {
       const float hi = float(u);
-      bc.m2[r] = hi;
-      bc.m2_lo[r] = float(u - double(hi));
+      R.x = hi;
+      R.y = float(u - double(hi));
     } else {
-      bc.m2[r] = T(u);
-      bc.m2_lo[r] = T(0);
+      R.x = T(u);
+      R.y = T(0);
     }
-    bc.kappa[r] = T(kap);
-    bc.kappa_lo[r] = T(kap - double(T(kap)));
+    R.z = T(kap);
+    R.w = T(kap - double(T(kap)));
+    bc.res[r] = R;
   }
   if (RES_GRAD && tid >= 128 && tid < 128 + NR) {
     const int r = tid - 128;
@@ -206,10 +208,7 @@ __device__ inline void derive_compute(const ModelConst& km, CtaConst& cc, BlockC
     const double ig = mg > 0 ? rcp<double>(mg) : INFINITY;
     bc.tlim[0] = static_cast<unsigned long long>(__double_as_longlong(0.04 * ig));
     bc.tlim[1] = static_cast<unsigned long long>(__double_as_longlong(0.2 * ig));
-    bc.alpha = T(cc.alpha);
-    bc.beta = T(cc.beta);
-    bc.gc = T(cc.gc);
-    bc.dc = T(cc.dc);
+    bc.mix = Quad<T>{T(cc.alpha), T(cc.beta), T(cc.gc), T(cc.dc)};
   }
 }
 
@@ -729,10 +728,11 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
             // n = alpha|A|^2 + beta|Abar|^2 - 2 gc Re(A Abar*) - 2 dc Im(A Abar*);
             // dn = 2 Re(uA dA + uB dAbar), uA = alpha A* - (gc - i dc) Abar*,
             // uB = beta Abar* - (gc + i dc) A*.
-            const T uAr = bc.alpha * Ar - bc.gc * Br + bc.dc * Bi;
-            const T uAi = -bc.alpha * Ai + bc.gc * Bi + bc.dc * Br;
-            const T uBr = bc.beta * Br - bc.gc * Ar - bc.dc * Ai;
-            const T uBi = -bc.beta * Bi + bc.gc * Ai - bc.dc * Ar;
+            const Quad<T> M = bc.mix;  // {alpha, beta, gc, dc}
+            const T uAr = M.x * Ar - M.z * Br + M.w * Bi;
+            const T uAi = -M.x * Ai + M.z * Bi + M.w * Br;
+            const T uBr = M.y * Br - M.z * Ar - M.w * Ai;
+            const T uBi = -M.y * Bi + M.z * Ai - M.w * Ar;
             ev.template backprop_lineshapes<WEIGHTED>(src, bc, uAr, uAi, uBr, uBi, w, s1, s2);
           }
         }
