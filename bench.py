@@ -39,7 +39,7 @@ MODEL = "d0_k3pi_full"
 N_DATA, N_MC = 50_000, 1_000_000
 WORKLOAD_ID = 1              # seed key of this workload
 REF_SAMPLE = (2_500, 50_000)  # bounded oracle sample (data, MC) per reference step
-CPU_SAMPLE = (5_000, 100_000)  # bounded oracle sample for the cpu_baseline field
+CPU_SAMPLE = (10_000, 200_000)  # bounded oracle sample for the cpu_baseline field (~10-15 s of CPU work)
 
 
 def parse():
@@ -468,7 +468,7 @@ def run_tdmix(args):
         mc2 = smp.flat_phase_space(2_000_000, smp.rng(WORKLOAD_ID, 40 + rank))
         out["toy_study"] = {prec: run_toy_study(prec, data, t, mc2, args.toys) for prec in ("fp32", "fp64")}
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = time_oracle(data, t, mc, CPU_SAMPLE, evals=5, warmup=1)
+        out["cpu_baseline"] = time_oracle(data, t, mc, CPU_SAMPLE, evals=8, warmup=1)
     print(json.dumps(out), flush=True)
     return 0
 

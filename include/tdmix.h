@@ -148,6 +148,15 @@ int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, d
  * (re, im) pairs, row-major in (j, k). */
 int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
 
+/* Test hook for the bounded waits: while enabled, block 0 of every
+ * evaluation kernel does not issue its first event-tile copy, so its wait for
+ * that tile gives up after one second and the evaluation reports
+ * TDMIX_ERR_TIMEOUT (host outputs; NaN values with device outputs).  The
+ * kernel then returns normally and the context stays usable; the component
+ * cache and stored normalisation are marked stale.  Nothing faults or hangs:
+ * every wait in the kernels is bounded.  Off by default. */
+int tdmix_test_withhold_copy(tdmix_ctx* ctx, int enable);
+
 /* Kernel classes timed by tdmix_profile. */
 enum {
   TDMIX_PROF_EVAL = 0,       /* one evaluation: per-evaluation constants, data tiles (components or

@@ -62,6 +62,7 @@ struct tdmix_ctx {
   std::vector<int> floating;
   std::vector<double> last_res;
   bool cache_valid = false, gram_valid = false;
+  bool withhold_first_copy = false;  // test hook (tdmix_test_withhold_copy)
   std::string err;
   // kernel profiling: CUDA event pairs per kernel class, recorded on the stream
   bool prof_on = false;
@@ -376,6 +377,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.out_nll = out_nll;
   a.out_grad = out_grad;
   a.logtab = ctx->d_logtab;
+  a.withhold_first_copy = ctx->withhold_first_copy ? 1 : 0;
   a.sum_t = ctx->sum_t;
   a.inv_sum_w = ctx->inv_sum_w;
   a.trace = ctx->d_trace;
@@ -602,7 +604,9 @@ int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* gra
     TDMIX_CK(cudaStreamSynchronize(st));
     *nll_out = ctx->h_result[0];
     if (grad_out) std::memcpy(grad_out, ctx->h_result + kResHeader, np * sizeof(double));
-    return result_status(ctx);
+    const int st = result_status(ctx);
+    if (st == TDMIX_ERR_TIMEOUT) ctx->cache_valid = ctx->gram_valid = false;  // partial sums incomplete
+    return st;
   }
   // device outputs: written by the kernel itself, nothing else is enqueued
   return enqueue_eval(ctx, params, host_params, grad_out != nullptr, nullptr, ctx->d_result, nll_out, grad_out);
@@ -683,6 +687,12 @@ int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, in
       ctx->prof_n[c] = 0;
     }
   }
+  return TDMIX_OK;
+}
+
+int tdmix_test_withhold_copy(tdmix_ctx* ctx, int enable) {
+  if (!ctx) return TDMIX_ERR_ARG;
+  ctx->withhold_first_copy = enable != 0;
   return TDMIX_OK;
 }
 

@@ -79,6 +79,8 @@ struct EvalArgs {
   unsigned long long* trace;  // optional: per block kTracePhases globaltimer stamps (ns)
   const int64_t* mc_ranges;   // [grid + 1]: block b takes MC tiles [mc_ranges[b], mc_ranges[b + 1])
   const void* logtab;         // logarithm table: double2 {1/F, ln F}, F = 1 + j/128, j = 0..128
+  int withhold_first_copy;    // test hook: block 0 does not issue its first tile copy, so its
+                              // bounded wait for that tile runs out (TDMIX_ERR_TIMEOUT)
 };
 
 // Phases stamped by the evaluation kernel when tracing is on: start,

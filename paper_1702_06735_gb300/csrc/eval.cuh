@@ -124,11 +124,17 @@ __device__ __forceinline__ void mixing_trig(double a, double b, int tier, double
 // absolute accuracy).  Positive normal v only (the library function takes
 // the rest).
 constexpr int kLogTable = 129;
-__device__ __forceinline__ double log_table(double v, const double2* tab) {
+constexpr double kLn2 = 0.69314718055994530942;
+// ln v = e ln 2 + the returned value (the caller sums the exponents as
+// integers and multiplies by ln 2 once).
+__device__ __forceinline__ double log_table_split(double v, const double2* tab, int& e) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
-  if (bits - 0x0010000000000000ull >= 0x7FE0000000000000ull) return log(v);  // not positive normal
+  if (bits - 0x0010000000000000ull >= 0x7FE0000000000000ull) {  // not positive normal
+    e = 0;
+    return log(v);
+  }
   const unsigned long long frac = bits & 0x000FFFFFFFFFFFFFull;
-  const int e = int(bits >> 52) - 1023;
+  e = int(bits >> 52) - 1023;
   const double m = __longlong_as_double(static_cast<long long>(frac | 0x3FF0000000000000ull));
   const unsigned long long j = (frac + (1ull << 44)) >> 45;  // nearest multiple of 1/128, 0 .. 128
   const double F = __longlong_as_double(static_cast<long long>(0x3FF0000000000000ull + (j << 45)));  // 1 + j/128
@@ -136,7 +142,13 @@ __device__ __forceinline__ double log_table(double v, const double2* tab) {
   const double r = (m - F) * t.x;
   const double p = fma(r, fma(r, fma(r, fma(r, -1.0 / 6, 1.0 / 5), -1.0 / 4), 1.0 / 3), -0.5);
   const double l1p = fma(r * r, p, r);
-  return fma(double(e), 0.69314718055994530942, t.y + l1p);
+  return t.y + l1p;
+}
+
+__device__ __forceinline__ double log_table(double v, const double2* tab) {
+  int e;
+  const double m = log_table_split(v, tab, e);
+  return fma(double(e), kLn2, m);
 }
 
 // Single-precision version for |a|, |b| <= 0.1 (Maclaurin series through the
@@ -324,7 +336,8 @@ struct EventCore {
 // One data event's rate from its amplitudes A, Abar (working precision) and
 // decay time: Eq. (mix) as B = 2 |cosh(w) A - sinh(w) Abar|^2 with
 // w = (y + i x) Gamma t / 2, in double precision.  For a B that is positive
-// and finite, adds ln B to lnb and returns true; with GRAD it also forms the
+// and finite, adds ln B to the pair (lnb, lexp) as lnb + lexp ln 2 and
+// returns true; with GRAD it also forms the
 // sensitivities of ln B: d ln B = 2 Re(tA dA + tB dAbar) and adds
 // d ln B / dx, d ln B / dy to gx, gy.  d ln B = 2 Re(V dZ), V = Z* / |Z|^2,
 // dZ = cosh(w) dA - sinh(w) dAbar + (sinh(w) A - cosh(w) Abar) dw,
@@ -335,7 +348,7 @@ struct EventCore {
 template <class P, bool GRAD>
 __device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, const double2* logtab,
                                           typename P::T Ar_, typename P::T Ai_, typename P::T Br_,
-                                          typename P::T Bi_, double t_e, double& lnb, double* rate,
+                                          typename P::T Bi_, double t_e, double& lnb, int& lexp, double* rate,
                                           typename P::T& tAr, typename P::T& tAi, typename P::T& tBr,
                                           typename P::T& tBi, typename P::T& gx, typename P::T& gy) {
   using T = typename P::T;
@@ -349,11 +362,13 @@ __device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, c
   const double shr = sha * cb, shi = cha * sb;  // sinh(w)
   const double Zr = chr * Ar - chi * Ai - (shr * Br - shi * Bi);
   const double Zi = chr * Ai + chi * Ar - (shr * Bi + shi * Br);
-  const double B = 2.0 * (Zr * Zr + Zi * Zi);
-  if (rate) *rate = exp(-gt) * B;
-  const unsigned long long bb = static_cast<unsigned long long>(__double_as_longlong(B));
+  const double z2 = Zr * Zr + Zi * Zi;  // B = 2 z2: ln B = ln z2 + ln 2
+  if (rate) *rate = exp(-gt) * (2.0 * z2);
+  const unsigned long long bb = static_cast<unsigned long long>(__double_as_longlong(z2));
   if (bb - 1ull >= 0x7FEFFFFFFFFFFFFFull) return false;  // B <= 0, infinite or NaN
-  lnb += log_table(B, logtab);
+  int e;
+  lnb += log_table_split(z2, logtab, e);
+  lexp += e + 1;
   if constexpr (GRAD) {
     T cr, ci, sr, si, Zrt, Zit, tg;
     if constexpr (P::kF32) {

@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
     derive_compute<T, U, NR>(a.km, cc, bc);
     __syncthreads();
 
-    double lnb = 0.0;
-    int bad = 0;
+    double lnb = 0.0;  // sum ln B = lnb + lexp ln 2
+    int bad = 0, lexp = 0;
     T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
         T Ar_, Ai_, Br_, Bi_;
         ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
         T tAr, tAi, tBr, tBi;
-        if (mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, t_e, lnb, nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
+        if (mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp, nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
           if constexpr (GRAD) {
 #pragma unroll
             for (int k = 0; k < U; ++k) {
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
     }
     // chunk partial -> its row (double-float; see block_sum_df)
     {
-      const double v0 = warp_sum(lnb);
+      const double v0 = warp_sum(fma(double(lexp), kLn2, lnb));
       const int v1 = warp_sum(bad);
       if (lane == 0) {
         red_lnb[warp] = v0;

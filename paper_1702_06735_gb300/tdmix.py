@@ -33,6 +33,7 @@ _SIGNATURES = {
     "tdmix_chain_component": (_c_i, [_c_p, _c_i]),
     "tdmix_default_params": (_c_i, [_c_p, _c_p]),
     "tdmix_set_floating": (_c_i, [_c_p, _c_p]),
+    "tdmix_test_withhold_copy": (_c_i, [_c_p, _c_i]),
     "tdmix_load_events": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_nll": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
     "tdmix_event_rates": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
@@ -236,6 +237,11 @@ class TDMix:
         out = np.empty(2 * U * U)
         self._check(self._lib.tdmix_norm_matrix(self._ctx, out.ctypes.data))
         return (out[0::2] + 1j * out[1::2]).reshape(U, U)
+
+    def test_withhold_copy(self, enable: bool = True):
+        """Test hook: block 0 withholds its first tile copy, so its bounded
+        wait runs out and evaluations report TDMIX_ERR_TIMEOUT."""
+        self._check(self._lib.tdmix_test_withhold_copy(self._ctx, int(enable)))
 
     PROF_CLASSES = ("eval", "precompute")
 
