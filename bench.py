@@ -39,7 +39,7 @@ MODEL = "d0_k3pi_full"
 N_DATA, N_MC = 50_000, 1_000_000
 WORKLOAD_ID = 1              # seed key of this workload
 REF_SAMPLE = (2_500, 50_000)  # bounded oracle sample (data, MC) per reference step
-CPU_SAMPLE = (10_000, 200_000)  # bounded oracle sample for the cpu_baseline field (~10-15 s of CPU work)
+CPU_SAMPLE = (25_000, 500_000)  # bounded oracle sample for the cpu_baseline field (~10 s of CPU work)
 
 
 def parse():
@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="tdmix", choices=["tdmix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--toys", type=int, default=32, help="pseudo-experiments in the serving toy study (0: skip)")
+    ap.add_argument("--no-paper-fit", dest="paper_fit", action="store_false",
+                    help="skip the fit benchmark of the paper's timing table (100k events, 0.75M-6M MC)")
     ap.add_argument("--flush-l2", action="store_true",
                     help="write 256 MB between timed steps (default: none; the inputs of one evaluation exceed L2)")
     ap.add_argument("--quick", action="store_true",
@@ -290,6 +292,64 @@ def run_toy_study(precision, pool_p4, pool_t, mc, n_toys, budget_fraction=0.4, c
 
 
 # ----------------------------------------------------------------------------
+# the paper's fit benchmark (Sec. 5, timing table): 100,000 pseudo-events,
+# fixed model, x and y floating, MC normalisation samples of 0.75M - 6M points
+# ----------------------------------------------------------------------------
+def run_paper_fit_benchmark(dev, precision="fp32", mc_sizes=(750_000, 1_500_000, 3_000_000, 6_000_000)):
+    """Wall time of a complete x, y fit (BFGS, strong-Wolfe line search,
+    MINUIT-style distance-to-minimum stop) per normalisation-sample size,
+    including the first evaluation that computes the normalisation matrix.
+    The paper's table reports the same fit on its hardware (other hardware,
+    unstated precision): context, not a target."""
+    import torch
+    from paper_1702_06735_gb300 import minimize, samples
+    from paper_1702_06735_gb300.tdmix import TDMix, TDMixError
+
+    gen = TDMix(MODEL, "fp64")
+    one = samples.flat_phase_space(1, samples.rng(WORKLOAD_ID, 99))
+    p0 = gen.default_params()
+
+    def rate(p4, t):
+        gen.load_events(p4, t, one)
+        r, _ = gen.event_rates(p0)
+        return r
+    data, t, _ = samples.generate_time_dependent(100_000, samples.rng(WORKLOAD_ID, 31), rate, 1.0 / samples.TAU_D,
+                                                 float(p0[-1]), pilot=200_000, batch=1 << 18)
+    gen.close()
+    mc_all = samples.flat_phase_space(max(mc_sizes), samples.rng(WORKLOAD_ID, 32))
+    mask = np.zeros(len(p0), dtype=bool)
+    mask[-2:] = True
+    scale = np.ones(len(p0))
+    scale[-2:] = 1e-3
+    out = []
+    for n_mc in mc_sizes:
+        c = TDMix(MODEL, precision)
+        c.load_events(torch.from_numpy(data).to(dev), torch.from_numpy(t).to(dev),
+                      torch.from_numpy(mc_all[:n_mc]).to(dev))
+        c.set_floating(mask.astype(np.int32))
+        x0 = p0.copy()
+        x0[-2] += 0.001
+        x0[-1] -= 0.001
+
+        def fg(p):
+            try:
+                return c.nll(p)
+            except TDMixError as e:
+                if e.code in (-5, -6):
+                    return float("inf"), np.full(len(p), np.nan)
+                raise
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = minimize.bfgs(fg, x0, floating=mask, scale=scale, gtol=1e-3, edm_tol=1e-6, max_iter=100)
+        wall = time.perf_counter() - t0
+        out.append({"mc_points": n_mc, "fit_s": wall, "evals": int(r.n_eval), "converged": bool(r.converged),
+                    "x": float(r.x[-2]), "y": float(r.x[-1])})
+        c.close()
+    return {"data_events": len(t), "precision": precision, "fits": out,
+            "note": "fixed model, x and y floating; includes the evaluation that computes the normalisation"}
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def run_tdmix(args):
@@ -411,6 +471,11 @@ def run_tdmix(args):
     # components 304, A and Abar with low parts 256, fp32 Eq. (mix) adjoint 82,
     # gA/gB 128, adjoint 534 (Eq. (mix) itself is fp64 and not counted)
     FLOP_MC, FLOP_DATA = 1242, 1304
+    # DRAM bytes read + written by one launch of this kernel in the steady
+    # state of this command (ncu --cache-control none, the second of two
+    # captured launches: 141.81 MB + 4.37 MB; the summary is committed with
+    # the profiles); None once the kernel changes after that capture
+    TRAFFIC_BYTES = 146.18e6
     flops_per_launch = N_MC * FLOP_MC + N_DATA * FLOP_DATA
     ev_ms, ev_n = prof32["eval"]
     ev_launch_ms = ev_ms / ev_n
@@ -450,7 +515,7 @@ def run_tdmix(args):
         "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof32.items()},
         "roofline": {"kernel": "k_eval (one full evaluation, fp32 path)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "traffic": TRAFFIC_BYTES, "algorithmic_bytes_per_launch": bytes_per_launch,
                      "launch_ms": ev_launch_ms,
                      "alu": {"achieved": alu_tflops, "peak": ALU_PEAK, "unit": "TFLOP/s", "frac": alu_tflops / ALU_PEAK,
                              "algorithmic_flops_per_launch": flops_per_launch,
@@ -463,6 +528,8 @@ def run_tdmix(args):
         "generation": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in gen_stats.items()},
         "wall_s_timed_region": wall32,
     }
+    if args.paper_fit and not args.quick:
+        out["paper_fit_benchmark"] = run_paper_fit_benchmark(dev)
     if args.toys > 0:
         from paper_1702_06735_gb300 import samples as smp
         mc2 = smp.flat_phase_space(2_000_000, smp.rng(WORKLOAD_ID, 40 + rank))

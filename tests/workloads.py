@@ -59,3 +59,27 @@ def rate_scale(model, data, t, params):
     y = float(p[-1])
     gt = model.gamma * torch.as_tensor(t)
     return (2 * torch.exp(-gt) * torch.cosh(y * gt) * s ** 2).numpy()
+
+
+def rate_scale_terms(model, data, t, params):
+    """Like rate_scale, but the chain sum runs over every Bose ordering
+    separately: 2 e^{-G t} cosh(y G t) (sum_i sum_o |c_i T_i,o|)^2.  It also
+    bounds cancellations between the two orderings of one chain, which
+    rate_scale (built on the Bose-summed chain amplitudes) does not see."""
+    p = torch.as_tensor(params, dtype=torch.float64)
+    coef, m0, g0, _, _ = tdamp._unpack(model, p)
+    ev = torch.as_tensor(data, dtype=torch.float64)
+    perm = list(range(ev.shape[1]))
+    if model.bose is not None:
+        i, j = model.bose
+        perm[i], perm[j] = perm[j], perm[i]
+    ev_swap = ev[:, perm, :]
+    s = torch.zeros(ev.shape[0], dtype=torch.float64)
+    for k, ch in enumerate(model.chains):
+        s = s + coef[k].abs() * tdamp._chain_one_order(model, ch, ev, m0, g0).abs()
+        if model.bose is not None:
+            s = s + coef[k].abs() * tdamp._chain_one_order(model, ch, ev_swap, m0, g0).abs()
+    y = float(p[-1])
+    gt = model.gamma * torch.as_tensor(t)
+    return (2 * torch.exp(-gt) * torch.cosh(y * gt) * s ** 2).numpy()
+
