@@ -68,3 +68,14 @@ def test_null_arguments(lib):
     assert lib.tdmix_nll(None, None, None, None) == -1
     assert lib.tdmix_num_params(None) == -1
     assert lib.tdmix_last_error(None) == b"null context"
+
+
+def test_model_beyond_the_compiled_specialisations_is_refused(lib):
+    """16 components (the full model without shared blocks) exceed the
+    register-Gram limit of this build: creation reports TDMIX_ERR_UNSUPPORTED
+    (before any device call) with a message, instead of a slower path."""
+    from paper_1702_06735_gb300.tdmix import TDMix, TDMixError
+    with pytest.raises(TDMixError) as e:
+        TDMix("d0_k3pi_full_nodedup", "fp32")
+    assert e.value.code == -8
+    assert "not compiled" in str(e.value)
