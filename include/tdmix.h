@@ -200,8 +200,8 @@ int tdmix_server_create(const char* model_json, int precision, size_t hbm_budget
 /* The shared phase-space MC sample (host or device memory, see
  * tdmix_events); computes the normalisation sums of the fixed model. */
 int tdmix_server_add_mc(tdmix_server* s, const tdmix_events* mc);
-/* Registers a data sample (copied to host memory; admitted to the device on
- * demand); *sample_id receives its id. */
+/* Registers a data sample (copied to page-locked host memory; admitted to the
+ * device on demand, and again after an eviction); *sample_id receives its id. */
 int tdmix_server_add_sample(tdmix_server* s, const tdmix_events* data, int* sample_id);
 /* Queues an NLL + gradient evaluation of sample_id at params (host,
  * num_params doubles; masses and widths must equal the model's values,

@@ -50,10 +50,41 @@ namespace {
 
 double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
 
+// Page-locked host array (cudaMallocHost), so that the copies of a sample at
+// each (re-)admission run at the full rate of the host link.
+struct PinnedDoubles {
+  double* p = nullptr;
+  PinnedDoubles() = default;
+  PinnedDoubles(const PinnedDoubles&) = delete;
+  PinnedDoubles& operator=(const PinnedDoubles&) = delete;
+  PinnedDoubles(PinnedDoubles&& o) noexcept : p(o.p) { o.p = nullptr; }
+  PinnedDoubles& operator=(PinnedDoubles&& o) noexcept {
+    if (this != &o) {
+      reset();
+      p = o.p;
+      o.p = nullptr;
+    }
+    return *this;
+  }
+  ~PinnedDoubles() { reset(); }
+  cudaError_t alloc(size_t count) {
+    reset();
+    void* q = nullptr;
+    const cudaError_t e = cudaMallocHost(&q, count * sizeof(double));
+    if (e == cudaSuccess) p = static_cast<double*>(q);
+    return e;
+  }
+  void reset() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+  }
+  double* data() { return p; }
+};
+
 struct SampleRec {
   int64_t n = 0;
-  std::vector<double> planes;  // host copy [16][n] for (re-)admission
-  std::vector<double> t;
+  PinnedDoubles planes;  // host copy [16][n] for (re-)admission
+  PinnedDoubles t;
   bool resident = false;
   void* cache = nullptr;   // tile-major components and decay times
   int64_t tile_bytes = 0;
@@ -350,8 +381,8 @@ int tdmix_server_add_sample(tdmix_server* s, const tdmix_events* data, int* samp
   if (!s || !data || !sample_id || data->n < 1 || !data->t) return sfail(s, TDMIX_ERR_ARG, "bad sample");
   SampleRec rec;
   rec.n = data->n;
-  rec.planes.resize(size_t(16) * data->n);
-  rec.t.resize(data->n);
+  SV_CK(rec.planes.alloc(size_t(16) * data->n));
+  SV_CK(rec.t.alloc(size_t(data->n)));
   for (int a = 0; a < 4; ++a)
     for (int c = 0; c < 4; ++c) {
       double* dst = rec.planes.data() + size_t(a * 4 + c) * data->n;
