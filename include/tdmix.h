@@ -61,7 +61,7 @@ typedef enum {
   TDMIX_ERR_NONFINITE = -5, /* non-finite parameter, or a rate <= 0 / not finite */
   TDMIX_ERR_DOMAIN = -6,    /* |y| >= 1, mass or width <= 0, pole below threshold */
   TDMIX_ERR_TIMEOUT = -7,   /* a bounded wait gave up */
-  TDMIX_ERR_UNSUPPORTED = -8 /* model structure not compiled into this build */
+  TDMIX_ERR_UNSUPPORTED = -8 /* model structure not compiled into the library */
 } tdmix_status;
 
 typedef enum {
@@ -92,7 +92,7 @@ typedef struct {
  * shared (Sec. 3: recurring form factors, spin factors and lineshapes are
  * linked to one instance).  *out receives the context; TDMIX_ERR_ARG for an
  * invalid model, TDMIX_ERR_UNSUPPORTED if its structure was not compiled
- * into this build. */
+ * into the library. */
 int tdmix_create(const char* model_json, int precision, tdmix_ctx** out);
 
 /* Uses the given cudaStream_t (NULL: the legacy default stream) for all

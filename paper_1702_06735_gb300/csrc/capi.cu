@@ -509,7 +509,7 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   *out = ctx;
   if (!ctx->ops)
     return fail(ctx, TDMIX_ERR_UNSUPPORTED,
-                "model structure not compiled into this build (add the model file and rebuild): " +
+                "model structure not compiled into the library (add the model file and rebuild): " +
                     ctx->model.signature());
   TDMIX_CK(cudaGetDevice(&ctx->device));
   TDMIX_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));

@@ -72,7 +72,7 @@ def test_null_arguments(lib):
 
 def test_model_beyond_the_compiled_specialisations_is_refused(lib):
     """16 components (the full model without shared blocks) exceed the
-    register-Gram limit of this build: creation reports TDMIX_ERR_UNSUPPORTED
+    register-Gram limit of the compiled library: creation reports TDMIX_ERR_UNSUPPORTED
     (before any device call) with a message, instead of a slower path."""
     from paper_1702_06735_gb300.tdmix import TDMix, TDMixError
     with pytest.raises(TDMixError) as e:
