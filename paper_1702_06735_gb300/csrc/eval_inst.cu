@@ -1,5 +1,6 @@
 // Instantiates the per-event kernels for every compiled model structure in
 // one precision (TDMIX_PREC_F32 = 0: fp64 path, 1: fp32 precision path).
+#include <atomic>
 #include <string>
 
 #include "fused.cuh"
@@ -27,19 +28,36 @@ namespace {  // internal linkage: this file is compiled once per precision
 // many components.
 constexpr int kMaxRegisterGramU = 8;
 
+constexpr int kMaxDevices = 64;
+
+// Raises the dynamic shared-memory limit of kernel `f` to `smem` bytes on the
+// current device once (cudaFuncSetAttribute acts per device); `seen` holds
+// the largest size allowed so far per device.  Safe to call from several
+// host threads.
+template <class F>
+cudaError_t allow_smem(F* f, int smem, std::atomic<int> (&seen)[kMaxDevices]) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem <= seen[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int cur = seen[dev].load(std::memory_order_relaxed);
+  while (cur < smem && !seen[dev].compare_exchange_weak(cur, smem, std::memory_order_release)) {
+  }
+  return cudaSuccess;
+}
+
 template <class S>
 struct Ops {
   static constexpr bool kOk = S::U <= kMaxRegisterGramU;
   template <bool FULL, bool GRAD, bool W>
   static cudaError_t launch(int grid, cudaStream_t st, const EvalArgs& a) {
     const int smem = Layout<Prec, S>::smem_bytes(FULL, int(a.ld));
-    static int attr_set = 0;  // per instantiation: the largest size allowed so far
-    if (smem > attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k_eval<Prec, S, FULL, GRAD, W>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return e;
-      attr_set = smem;
-    }
+    static std::atomic<int> seen[kMaxDevices];  // per instantiation and device
+    const cudaError_t e = allow_smem(k_eval<Prec, S, FULL, GRAD, W>, smem, seen);
+    if (e != cudaSuccess) return e;
     k_eval<Prec, S, FULL, GRAD, W><<<grid, kTile, smem, st>>>(a);
     return cudaGetLastError();
   }
@@ -57,15 +75,10 @@ struct Ops {
   static cudaError_t serve(bool grad, int grid, cudaStream_t st, const ServeArgs& a) {
     if constexpr (kOk) {
       const int smem = ServeLayout<Prec, S>::smem_bytes();
-      static bool attr = false;
+      static std::atomic<int> seen_g[kMaxDevices], seen_n[kMaxDevices];
       auto kern = grad ? k_serve<Prec, S, true> : k_serve<Prec, S, false>;
-      if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_serve<Prec, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(k_serve<Prec, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-      }
+      const cudaError_t e = allow_smem(kern, smem, grad ? seen_g : seen_n);
+      if (e != cudaSuccess) return e;
       kern<<<grid, kTile, smem, st>>>(a);
       return cudaGetLastError();
     }
