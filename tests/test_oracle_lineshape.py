@@ -95,3 +95,82 @@ def test_breakup_momentum_two_body_closed_form():
     q = tdamp.breakup_q2(s, M_K ** 2, M_PI ** 2).sqrt()
     e = torch.sqrt(q * q + M_K ** 2) + torch.sqrt(q * q + M_PI ** 2)
     assert torch.allclose(e, s.sqrt(), rtol=1e-14, atol=0)
+
+
+def _phase_space_density(s, ma, mb):
+    """Two-body phase-space density of a system of mass sqrt(s) decaying to
+    masses ma, mb, up to a constant: in the rest frame
+    Phi_2 = int d^3p / (4 E_a E_b) delta(sqrt(s) - E_a - E_b)
+          = 4 pi p^2 / (4 E_a E_b |d(E_a + E_b)/dp|) at the root p = q.
+    The root is found by bisection on energy conservation and the Jacobian
+    by a central difference, so neither uses a closed form of q."""
+    rs = math.sqrt(s)
+
+    def etot(p):
+        return math.sqrt(p * p + ma * ma) + math.sqrt(p * p + mb * mb)
+    lo, hi = 0.0, rs
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if etot(mid) < rs:
+            lo = mid
+        else:
+            hi = mid
+    q = 0.5 * (lo + hi)
+    h = 1e-6 * q
+    jac = (etot(q + h) - etot(q - h)) / (2 * h)
+    ea, eb = math.sqrt(q * q + ma * ma), math.sqrt(q * q + mb * mb)
+    return math.pi * q * q / (ea * eb * jac), q
+
+
+def _penetration(L, z):
+    """von Hippel-Quigg centrifugal-barrier penetration factors B_L(z)^2
+    (Phys. Rev. D 5 (1972) 624), including their q^(2L) behaviour."""
+    return {0: 1.0, 1: 2 * z / (1 + z), 2: 13 * z * z / (9 + 3 * z + z * z)}[L]
+
+
+@pytest.mark.parametrize("L,m0,g0,dm", [
+    (1, 0.89555, 0.0473, (M_K, M_PI)),    # K*(892) -> K pi
+    (1, 0.77526, 0.1491, (M_PI, M_PI)),   # rho(770) -> pi pi
+    (2, 1.2755, 0.1867, (M_PI, M_PI)),    # a D-wave resonance -> pi pi
+])
+@pytest.mark.parametrize("sqrt_s_over_m0", [0.8, 0.93, 1.07, 1.4])
+def test_mdw_width_off_pole_is_phase_space_times_barrier(L, m0, g0, dm, sqrt_s_over_m0):
+    """Away from the pole the mass-dependent width is the pole width scaled
+    by the two-body phase-space density and by the centrifugal-barrier
+    penetration of the partial wave L:
+        Gamma(s) / Gamma0 = [Phi_2(s) / Phi_2(m0^2)] [B_L(q r)^2 / B_L(q0 r)^2].
+    Phi_2 ~ q / sqrt(s) carries the factor m0 / sqrt(s) and one power of
+    q / q0; B_L^2 ~ q^(2L) F_L^2 carries the rest.  A width with sqrt(s)/m0
+    in place of m0/sqrt(s), or with an unsquared barrier ratio, fails here
+    (both differ by tens of percent at these points)."""
+    r = 1.5
+    s = (sqrt_s_over_m0 * m0) ** 2
+    if math.sqrt(s) <= dm[0] + dm[1]:
+        pytest.skip("below threshold")
+    phi, q = _phase_space_density(s, *dm)
+    phi0, q0 = _phase_space_density(m0 * m0, *dm)
+    expected = g0 * (phi / phi0) * _penetration(L, (q * r) ** 2) / _penetration(L, (q0 * r) ** 2)
+    got = float(tdamp.mass_dependent_width(torch.tensor(s, dtype=F64), torch.tensor(m0, dtype=F64),
+                                           torch.tensor(g0, dtype=F64), L, *dm, r))
+    assert abs(got / expected - 1) < 1e-8, (got, expected)
+    # the two plausible mistakes are far outside the tolerance at these points
+    swapped = got * s / (m0 * m0)
+    unsquared = got * math.sqrt(_penetration(L, (q0 * r) ** 2) / _penetration(L, (q * r) ** 2)
+                                * (q / q0) ** (2 * L))
+    assert abs(swapped / expected - 1) > 1e-3 and abs(unsquared / expected - 1) > 1e-3
+
+
+def test_mdw_width_values_k_star():
+    """Literal values for K*(892) -> K pi (L = 1, r = 1.5 GeV^-1), worked by
+    hand from energy conservation, E_K = (s + m_K^2 - m_pi^2) / (2 sqrt s),
+    q^2 = E_K^2 - m_K^2: at the pole (m0 = 0.89555 GeV) q0 = 0.290823 GeV;
+    at sqrt(s) = 0.80 GeV, q = 0.219187 GeV and
+    Gamma = 0.0473 x (0.89555/0.80) x (q/q0)^3 x (1 + (q0 r)^2)/(1 + (q r)^2)
+          = 0.0473 x 1.119437 x 0.428116 x 1.074184 = 0.0243501 GeV;
+    at sqrt(s) = 1.00 GeV, q = 0.361901 GeV and
+    Gamma = 0.0473 x 0.89555 x 1.927007 x 0.919373 = 0.0750457 GeV."""
+    m0, g0 = 0.89555, 0.0473
+    for rs, want in ((0.80, 0.0243501), (1.00, 0.0750457)):
+        got = float(tdamp.mass_dependent_width(torch.tensor(rs * rs, dtype=F64), torch.tensor(m0, dtype=F64),
+                                               torch.tensor(g0, dtype=F64), 1, M_K, M_PI, 1.5))
+        assert abs(got / want - 1) < 5e-6, (rs, got, want)
