@@ -139,7 +139,10 @@ int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* gra
 
 /* Per-event rate e^{-Gamma t} B(e) of Eq. (mix) for every data event
  * (rates_out: host or device, n_data doubles) and, if norm_out is not NULL,
- * the normalisation N (one double, same memory kind as rates_out). */
+ * the normalisation N (one double, same memory kind as rates_out).  Always
+ * a full evaluation (no component cache), so on the fp32 path every rate
+ * is within 1e-5 relative of its double-precision value (see
+ * tdmix_recomputed_events). */
 int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, double* norm_out);
 
 /* Normalisation matrix I_jk = sum_e w_e a_j(e)^* a_k(e) / sum_e w_e of the
@@ -147,6 +150,17 @@ int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, d
  * recomputed it; I_out (host) receives U*U complex numbers as interleaved
  * (re, im) pairs, row-major in (j, k). */
 int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
+
+/* Number of data events the last evaluation recomputed in double-float
+ * (fp32 precision path only; 0 on the fp64 path).  The fp32 amplitudes
+ * carry rounding errors of a few ulps of the magnitude of their terms (the
+ * decay chains and Bose orderings summed coherently in A and Abar, Sec. 3),
+ * so an event whose amplitudes nearly cancel has a large relative error in
+ * its rate; a full evaluation recomputes every data event whose estimated
+ * term magnitude exceeds 16 times |cosh(w) A - sinh(w) Abar| (Eq. (mix) in
+ * factorised form) from double-float inputs.  Synchronises with the
+ * context's stream. */
+int tdmix_recomputed_events(tdmix_ctx* ctx, int64_t* n);
 
 /* Test hook for the bounded waits: while enabled, block 0 of every
  * evaluation kernel does not issue its first event-tile copy, so its wait for
@@ -156,6 +170,28 @@ int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
  * cache and stored normalisation are marked stale.  Nothing faults or hangs:
  * every wait in the kernels is bounded.  Off by default. */
 int tdmix_test_withhold_copy(tdmix_ctx* ctx, int enable);
+
+/* Self-test of the device arithmetic the kernels use in place of CUDA's
+ * functions (library extension for testing; the paper has no counterpart).
+ * Evaluates routine `which` on n host arguments `in` on the current device
+ * and writes n results to `out` (host; 4n for the mixing-series codes:
+ * cosh v, sinh v, cos v, sin v per argument).  Returns TDMIX_ERR_ARG for a
+ * bad code, n < 1 or a null pointer, TDMIX_ERR_NOMEM / TDMIX_ERR_CUDA on
+ * failure of its own allocations, copies or launch. */
+enum {
+  TDMIX_MATH_LOG_TABLE = 0, /* table-driven natural logarithm (Tang's method), positive normal v */
+  TDMIX_MATH_LOG_CUDA = 1,  /* CUDA's log, for comparison */
+  TDMIX_MATH_RCP_F64 = 2,   /* 1/v from the hardware approximation and two Newton steps */
+  TDMIX_MATH_DIV_F64 = 3,   /* IEEE double division 1.0 / v, for comparison */
+  TDMIX_MATH_RCP_F32 = 4,   /* 1/v in single precision: approximation and one Newton step */
+  TDMIX_MATH_DIV_F32 = 5,   /* IEEE single division 1.0f / v, for comparison */
+  TDMIX_MATH_DF_RCP = 6,    /* 1/v in double-float arithmetic (v split into two floats) */
+  TDMIX_MATH_MIX_TIER0 = 7, /* cosh, sinh, cos, sin by the series through z^3 (|v| <= 0.02) */
+  TDMIX_MATH_MIX_TIER1 = 8, /* the same through z^5 (|v| <= 0.1) */
+  TDMIX_MATH_MIX_TIER2 = 9, /* CUDA's cosh, sinh, cos, sin, for comparison */
+  TDMIX_MATH_CODES = 10
+};
+int tdmix_test_math(int which, int64_t n, const double* in, double* out);
 
 /* Kernel classes timed by tdmix_profile. */
 enum {
@@ -236,8 +272,11 @@ int tdmix_trace(tdmix_ctx* ctx, int enable);
  * TDMIX_TRACE_PHASES entries); synchronises with the context's stream. */
 int tdmix_trace_read(tdmix_ctx* ctx, unsigned long long* stamps, int* n_blocks);
 
-/* Allocation-free evaluation of sum_e ln B(e) (B from Eq. (mix) as above,
- * without e^{-Gamma t}) over a component cache the caller keeps itself.
+/* Allocation-free evaluation of sum_e ln B(e) over a component cache the
+ * caller keeps itself, where for each event
+ *   B = 2 |cosh(w) A - sinh(w) Abar|^2,  w = (y + i x) gamma t / 2,
+ *   A = sum_j cA_j a_j,  Abar = sum_j cB_j a_j
+ * (the decay-time dependence of the rate without its e^{-gamma t} factor).
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory while they evaluate, such as work being recorded into a CUDA
  * graph, code running under an external memory manager that owns every

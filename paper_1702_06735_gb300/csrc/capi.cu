@@ -52,6 +52,7 @@ struct tdmix_ctx {
   int64_t* d_ranges = nullptr;            // per-block MC tile ranges [num_sms + 1]
   double* d_logtab = nullptr;             // logarithm table of the kernels ({1/F, ln F} pairs)
   int64_t ranges_key[3] = {-1, -1, -1};   // (data tiles, MC tiles, grid) the ranges were made for
+  double* last_result = nullptr;   // result vector the last evaluation wrote (d_result or d_result_map)
   double* h_result = nullptr;      // pinned, mapped: written by the kernel for host callers
   double* d_result_map = nullptr;  // device address of h_result
   void* d_part = nullptr;         // block partials of the evaluation kernel (float2 [num_sms][width])
@@ -168,9 +169,11 @@ ModelConst make_model_const(const CompiledModel& m, const std::vector<int>& floa
   return k;
 }
 
+}  // namespace
+
 // Table of the kernels' logarithm: {1/F_j, ln F_j} for F_j = 1 + j/128,
 // j = 0..128, each rounded once from extended precision.
-std::vector<double> make_log_table() {
+std::vector<double> tdmix::make_log_table() {
   std::vector<double> t(2 * 129);
   for (int j = 0; j <= 128; ++j) {
     const long double F = 1.0L + (long double)j / 128.0L;
@@ -179,6 +182,8 @@ std::vector<double> make_log_table() {
   }
   return t;
 }
+
+namespace {
 
 // Host-side screening of a parameter vector (host pointer only).
 int check_params(tdmix_ctx* ctx, const double* p) {
@@ -300,12 +305,19 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
         (rc = dalloc(ctx, s, reinterpret_cast<void**>(&s.rates), size_t(n) * sizeof(double))))
       return fail_clean(rc, ctx->err);
     cudaMemsetAsync(d.cache, 0, size_t(n_tiles) * d.cache_tile_bytes, st);
+    if (ctx->f32) {  // residuals of the width and spin x barrier factors (ill-conditioned events)
+      const CompiledModel& m = ctx->model;
+      void* lo = nullptr;
+      if ((rc = dalloc(ctx, s, &lo, size_t(n_tiles) * (m.NX() + m.U * m.NO) * kTileEvents * sizeof(float))))
+        return fail_clean(rc, ctx->err);
+      d.lo = static_cast<const float*>(lo);
+    }
   }
   int prc = prof_mark(ctx, TDMIX_PROF_PRECOMPUTE, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_clean(TDMIX_ERR_CUDA, std::string("before precompute: ") + cudaGetErrorString(e));
   launch_precompute(ctx->f32, mom, n, ctx->d_model, planes, d.tile_bytes, ops->n_planes, t_dev, w_dev, d.cache,
-                    d.cache_tile_bytes, st);
+                    d.cache_tile_bytes, const_cast<float*>(d.lo), st);
   e = cudaGetLastError();
   if (!prc) prc = prof_mark(ctx, TDMIX_PROF_PRECOMPUTE, 1);
   if (prc) {
@@ -351,7 +363,9 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   if (!ctx->data.loaded || !ctx->mc.loaded) return fail(ctx, TDMIX_ERR_STATE, "load data and MC events first");
   bool res_floating = false;
   for (int k = 2 * nc; k < 2 * nc + 2 * m.NR(); ++k) res_floating |= ctx->floating[k] != 0;
-  bool full = !host_params || !ctx->cache_valid || (want_grad && res_floating);
+  // per-event rates always come from a full evaluation (the recomputation
+  // of ill-conditioned events of the fp32 path runs there)
+  bool full = rates != nullptr || !host_params || !ctx->cache_valid || (want_grad && res_floating);
   if (host_params && !full) {
     for (int k = 0; k < 2 * m.NR(); ++k)
       if (params[2 * nc + k] != ctx->last_res[k]) full = true;
@@ -407,6 +421,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.mc_ranges = ctx->d_ranges;
 
   if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
+  ctx->last_result = result;
   TDMIX_CK(ctx->ops->eval(full, want_grad, grid, st, a));
   if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 1))) return rc;
   if (full) {
@@ -687,6 +702,17 @@ int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, in
       ctx->prof_n[c] = 0;
     }
   }
+  return TDMIX_OK;
+}
+
+int tdmix_recomputed_events(tdmix_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return fail(ctx, TDMIX_ERR_ARG, "null argument");
+  if (!ctx->last_result) return fail(ctx, TDMIX_ERR_STATE, "no evaluation yet");
+  TDMIX_CK(cudaStreamSynchronize(ctx->stream));
+  double v = 0;
+  if (ctx->last_result == ctx->d_result_map) v = ctx->h_result[4];
+  else TDMIX_CK(cudaMemcpy(&v, ctx->last_result + 4, sizeof(double), cudaMemcpyDeviceToHost));
+  *n = int64_t(v);
   return TDMIX_OK;
 }
 

@@ -49,6 +49,10 @@ constexpr int kTileEvents = 256;
 //           256 decay times (f64, data) or the 256 weights (T, weighted MC)
 //   cache:  (data) per tile the components [2U][256] (T: re planes, then im
 //           planes), then the 256 decay times (f64)
+//   lo:     (data, fp32 path) per tile the rounding residuals (value minus
+//           its float) of the width factors and spin x barrier factors,
+//           [NX + U*NO][256] floats; read only for the ill-conditioned
+//           events that are recomputed in double-float
 // The event slots of the last tile beyond n are zero.
 struct SampleDev {
   int64_t n, n_tiles;
@@ -56,6 +60,7 @@ struct SampleDev {
   int64_t tile_bytes;
   void* cache;
   int64_t cache_tile_bytes;
+  const float* lo;
   int weighted;
 };
 
@@ -71,7 +76,7 @@ struct EvalArgs {
   unsigned* counter;     // blocks finished (low 16 bits) and blocks that timed out
                          // (high bits); returned to 0 by the last block
   double* rates;         // optional: e^{-Gamma t} B per data event
-  double* result;        // [nll, N, n_bad or status, sum ln B, grad...]
+  double* result;        // [nll, N, n_bad or status, sum ln B, n recomputed, grad...]
   double* out_nll;       // optional second destination of the NLL
   double* out_grad;      // optional second destination of the gradient
   double sum_t;
@@ -123,7 +128,8 @@ struct ServeArgs {
   const void* logtab;       // logarithm table (as in EvalArgs)
 };
 
-// Result vector written by the evaluation kernel: [nll, N, n_bad or status, sum ln B, grad...]
-constexpr int kResHeader = 4;
+// Result vector written by the evaluation kernel:
+// [nll, N, n_bad or status, sum ln B, data events recomputed in double-float, grad...]
+constexpr int kResHeader = 5;
 
 }  // namespace tdmix

@@ -20,6 +20,7 @@
 
 #include "async_copy.cuh"
 #include "device_tables.hpp"
+#include "df.cuh"
 
 namespace tdmix {
 
@@ -230,11 +231,15 @@ struct EventCore {
     }
   }
 
-  template <class Src>
-  __device__ __forceinline__ void components(const Src& src) {
+  // With SCALE, sc[j] receives sum_o |K_{j,o}| (|Re P| + |Im P|) for the
+  // lineshape products P of component j: an upper bound (within a factor
+  // sqrt 2) of sum_o |K_{j,o} P|, the magnitude the rounding errors of a_j
+  // scale with.
+  template <bool SCALE = false, class Src>
+  __device__ __forceinline__ void components(const Src& src, T* sc = nullptr) {
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      T sr = 0, si = 0;
+      T sr = 0, si = 0, sm = 0;
 #pragma unroll
       for (int o = 0; o < NO; ++o) {
         const int t = j * NO + o;
@@ -253,9 +258,11 @@ struct EventCore {
         }
         sr = fma(K, pr, sr);
         si = fma(K, pi, si);
+        if constexpr (SCALE) sm = fma(fabs(K), fabs(pr) + fabs(pi), sm);
       }
       ar[j] = sr;
       ai[j] = si;
+      if constexpr (SCALE) sc[j] = sm;
     }
   }
 
@@ -333,8 +340,7 @@ struct EventCore {
   }
 };
 
-// One data event's rate from its amplitudes A, Abar (working precision) and
-// decay time: Eq. (mix) as B = 2 |cosh(w) A - sinh(w) Abar|^2 with
+// One data event's rate from its amplitudes A, Abar and decay time: Eq. (mix) as B = 2 |cosh(w) A - sinh(w) Abar|^2 with
 // w = (y + i x) Gamma t / 2, in double precision.  For a B that is positive
 // and finite, adds ln B to the pair (lnb, lexp) as lnb + lexp ln 2 and
 // returns true; with GRAD it also forms the
@@ -345,14 +351,16 @@ struct EventCore {
 // in the working precision; in fp32, cosh(w), sinh(w) and Z are re-derived
 // in fp32 rather than converted from their fp64 values.  `rate` (optional)
 // receives e^{-Gamma t} B.
+// Ar .. Bi are the amplitudes the rate is formed from (double precision);
+// Ar_ .. Bi_ the working-precision ones the sensitivities are formed from
+// (the same values unless the data event was recomputed in double-float).
 template <class P, bool GRAD>
-__device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, const double2* logtab,
-                                          typename P::T Ar_, typename P::T Ai_, typename P::T Br_,
-                                          typename P::T Bi_, double t_e, double& lnb, int& lexp, double* rate,
-                                          typename P::T& tAr, typename P::T& tAi, typename P::T& tBr,
+__device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, const double2* logtab, double Ar,
+                                          double Ai, double Br, double Bi, typename P::T Ar_, typename P::T Ai_,
+                                          typename P::T Br_, typename P::T Bi_, double t_e, double& lnb, int& lexp,
+                                          double* rate, typename P::T& tAr, typename P::T& tAi, typename P::T& tBr,
                                           typename P::T& tBi, typename P::T& gx, typename P::T& gy) {
   using T = typename P::T;
-  const double Ar = Ar_, Ai = Ai_, Br = Br_, Bi = Bi_;
   const double gt = bc.gamma * t_e;
   const unsigned long long tb = static_cast<unsigned long long>(__double_as_longlong(t_e));
   const int tier = tb <= bc.tlim[0] ? 0 : (tb <= bc.tlim[1] ? 1 : 2);  // t < 0 or NaN: tier 2
@@ -398,6 +406,110 @@ __device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, c
     gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
   }
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// Ill-conditioned data events of the fp32 path.
+//
+// The fp32 amplitudes carry rounding errors of a few ulps of the magnitudes
+// of their terms, S = sum over chains and Bose orderings of |c T|, so the
+// relative error of an event's rate grows like S / |Z| (Z = cosh(w) A -
+// sinh(w) Abar, B = 2 |Z|^2): about 5e-7 S / |Z| at worst.  Events whose
+// estimate of S / |Z| exceeds kRecomputeCond are recomputed: lineshapes,
+// components and A, Abar again in double-float from the double-float
+// inputs (invariants s = hi + lo in the tile; width and spin x barrier
+// factors from their hi planes in the tile and their lo planes in
+// SampleDev::lo; constants and coefficients as hi + lo pairs), which
+// leaves the rate within ~1e-12 of its value for any condition met in
+// practice.  Events below the threshold stay within 5e-7 x 16 = 8e-6.
+constexpr float kRecomputeCond = 16.0f;
+
+// Condition estimate of one fp32 data event: true if
+// S_Z > kRecomputeCond |Z|, with S_Z = cosh|w| S_A + sinh|w| S_B an upper
+// bound of the magnitude the errors of Z scale with (|cosh w| <= cosh|w|,
+// |sinh w| <= sinh|w|, |w| <= |a| + |b|) and Z formed in fp32.
+template <int U>
+__device__ __forceinline__ bool ill_conditioned(const BlockConst<float>& bc, const float (&sc)[U], float Ar, float Ai,
+                                                float Br, float Bi, double t_e) {
+  float SA = 0.f, SB = 0.f;
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const Quad<float> C = bc.cab[j];
+    SA = fmaf(fabsf(C.x) + fabsf(C.y), sc[j], SA);
+    SB = fmaf(fabsf(C.z) + fabsf(C.w), sc[j], SB);
+  }
+  const float tg = bc.gammaf * float(t_e);
+  const float a = 0.5f * bc.yf * tg, b = 0.5f * bc.xf * tg;
+  float cha, sha, cb, sb, chw, shw, c0, s0;
+  mixing_trig_f32(a, b, cha, sha, cb, sb);
+  mixing_trig_f32(fabsf(a) + fabsf(b), 0.f, chw, shw, c0, s0);
+  const float cr = cha * cb, ci = sha * sb, sr = sha * cb, si = cha * sb;
+  const float Zr = cr * Ar - ci * Ai - (sr * Br - si * Bi);
+  const float Zi = cr * Ai + ci * Ar - (sr * Bi + si * Br);
+  const float SZ = chw * SA + shw * SB;
+  return SZ * SZ > (kRecomputeCond * kRecomputeCond) * (Zr * Zr + Zi * Zi);
+}
+
+// A and Abar of one fp32 data event recomputed in double-float.  `stage`
+// is the event tile in shared memory (planes of SmemSrc), `lo` this tile's
+// lo planes ([NX + U NO][256] floats: width factors, then spin x barrier
+// factors), e the event's slot.  Out of line: it runs for few events, and
+// its registers must not add to the main loop's.
+template <class S>
+__device__ __noinline__ void df_amplitudes(const float* __restrict__ stage, const float* __restrict__ lo, int e,
+                                           const BlockConst<float>& bc, double* out) {
+  constexpr int TE = kTileEvents;
+  constexpr int NB = S::NB, NO = S::NO, U = S::U, NS = S::NS, NX = S::NX;
+  constexpr int X0 = 2 * NS, K0 = 2 * NS + NX;
+  DF bwr[NB > 0 ? NB : 1], bwi[NB > 0 ? NB : 1];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int r = S::bres(b), sp = S::bs(b), xp = S::bx(b);
+    const Quad<float> R = bc.res[r];
+    const DF delta = df_sub(DF{R.x, R.y}, DF{stage[sp * TE + e], stage[(NS + sp) * TE + e]});
+    const DF X = xp >= 0 ? DF{stage[(X0 + xp) * TE + e], lo[xp * TE + e]} : DF{1.0f, 0.0f};
+    const DF im = df_mul(DF{R.z, R.w}, X);
+    const DF inv = df_rcp(df_add(df_mul(delta, delta), df_mul(im, im)));
+    bwr[b] = df_mul(delta, inv);
+    bwi[b] = df_mul(im, inv);
+  }
+  DF Ar{0.f, 0.f}, Ai{0.f, 0.f}, Br{0.f, 0.f}, Bi{0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    DF sr{0.f, 0.f}, si{0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const int t = j * NO + o;
+      const int b0 = S::tb0(t), b1 = S::tb1(t);
+      const DF K{stage[(K0 + t) * TE + e], lo[(NX + t) * TE + e]};
+      DF pr, pi;
+      if (b0 >= 0 && b1 >= 0) {
+        pr = df_sub(df_mul(bwr[b0], bwr[b1]), df_mul(bwi[b0], bwi[b1]));
+        pi = df_add(df_mul(bwr[b0], bwi[b1]), df_mul(bwi[b0], bwr[b1]));
+      } else if (b0 >= 0) {
+        pr = bwr[b0];
+        pi = bwi[b0];
+      } else if (b1 >= 0) {
+        pr = bwr[b1];
+        pi = bwi[b1];
+      } else {
+        pr = DF{1.0f, 0.0f};
+        pi = DF{0.0f, 0.0f};
+      }
+      sr = df_add(sr, df_mul(K, pr));
+      si = df_add(si, df_mul(K, pi));
+    }
+    const Quad<float> C = bc.cab[j], L = bc.cab_lo[j];
+    const DF car{C.x, L.x}, cai{C.y, L.y}, cbr{C.z, L.z}, cbi{C.w, L.w};
+    Ar = df_add(Ar, df_sub(df_mul(car, sr), df_mul(cai, si)));
+    Ai = df_add(Ai, df_add(df_mul(car, si), df_mul(cai, sr)));
+    Br = df_add(Br, df_sub(df_mul(cbr, sr), df_mul(cbi, si)));
+    Bi = df_add(Bi, df_add(df_mul(cbr, si), df_mul(cbi, sr)));
+  }
+  out[0] = df_to_double(Ar);
+  out[1] = df_to_double(Ai);
+  out[2] = df_to_double(Br);
+  out[3] = df_to_double(Bi);
 }
 
 }  // namespace tdmix

@@ -1,6 +1,6 @@
 // Instantiates the per-event kernels for every compiled model structure in
 // one precision (TDMIX_PREC_F32 = 0: fp64 path, 1: fp32 precision path).
-#include <atomic>
+#include <mutex>
 #include <string>
 
 #include "fused.cuh"
@@ -30,40 +30,48 @@ constexpr int kMaxRegisterGramU = 8;
 
 constexpr int kMaxDevices = 64;
 
-// Raises the dynamic shared-memory limit of kernel `f` to `smem` bytes on the
-// current device once (cudaFuncSetAttribute acts per device); `seen` holds
-// the largest size allowed so far per device.  Safe to call from several
-// host threads.
+// Raises the dynamic shared-memory limit of kernel `f` to at least `smem`
+// bytes on the current device (cudaFuncSetAttribute acts per device); `seen`
+// holds the limit set so far per device.  Safe to call from several host
+// threads: the check, the attribute call and the update run under one
+// mutex per device, and the limit only ever grows (it is set to the larger
+// of the request and what was set before).
+struct SmemLimit {
+  std::mutex mu[kMaxDevices];
+  int seen[kMaxDevices] = {};
+};
+
 template <class F>
-cudaError_t allow_smem(F* f, int smem, std::atomic<int> (&seen)[kMaxDevices]) {
+cudaError_t allow_smem(F* f, int smem, SmemLimit& lim) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (smem <= seen[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> g(lim.mu[dev]);
+  if (smem <= lim.seen[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  int cur = seen[dev].load(std::memory_order_relaxed);
-  while (cur < smem && !seen[dev].compare_exchange_weak(cur, smem, std::memory_order_release)) {
-  }
+  lim.seen[dev] = smem;
   return cudaSuccess;
 }
 
 template <class S>
 struct Ops {
   static constexpr bool kOk = S::U <= kMaxRegisterGramU;
-  template <bool FULL, bool GRAD, bool W>
+  template <bool FULL, bool GRAD, bool W, bool RATES = false>
   static cudaError_t launch(int grid, cudaStream_t st, const EvalArgs& a) {
     const int smem = Layout<Prec, S>::smem_bytes(FULL, int(a.ld));
-    static std::atomic<int> seen[kMaxDevices];  // per instantiation and device
-    const cudaError_t e = allow_smem(k_eval<Prec, S, FULL, GRAD, W>, smem, seen);
+    static SmemLimit seen;  // per instantiation
+    const cudaError_t e = allow_smem(k_eval<Prec, S, FULL, GRAD, W, RATES>, smem, seen);
     if (e != cudaSuccess) return e;
-    k_eval<Prec, S, FULL, GRAD, W><<<grid, kTile, smem, st>>>(a);
+    k_eval<Prec, S, FULL, GRAD, W, RATES><<<grid, kTile, smem, st>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t eval(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a) {
     if constexpr (kOk) {
       const bool w = a.mc.weighted != 0;
+      if (a.rates && full && !grad)  // per-event rates (always a full evaluation without gradient)
+        return w ? launch<true, false, true, true>(grid, st, a) : launch<true, false, false, true>(grid, st, a);
       if (full) {
         if (grad) return w ? launch<true, true, true>(grid, st, a) : launch<true, true, false>(grid, st, a);
         return w ? launch<true, false, true>(grid, st, a) : launch<true, false, false>(grid, st, a);
@@ -75,7 +83,7 @@ struct Ops {
   static cudaError_t serve(bool grad, int grid, cudaStream_t st, const ServeArgs& a) {
     if constexpr (kOk) {
       const int smem = ServeLayout<Prec, S>::smem_bytes();
-      static std::atomic<int> seen_g[kMaxDevices], seen_n[kMaxDevices];
+      static SmemLimit seen_g, seen_n;
       auto kern = grad ? k_serve<Prec, S, true> : k_serve<Prec, S, false>;
       const cudaError_t e = allow_smem(kern, smem, grad ? seen_g : seen_n);
       if (e != cudaSuccess) return e;

@@ -275,7 +275,7 @@ struct Layout {
   static constexpr int U = S::U, NR = S::NR;
   static constexpr int NRE = U * (U + 1) / 2, NIM = U * (U - 1) / 2;
   static constexpr int WMC = 1 + NRE + NIM + 2 * NR;  // sum w, Re I (j<=k), Im I (j<k), s1, s2
-  static constexpr int WD = 4 + 4 * U + 2 * NR;       // sum ln B, n_bad, d/dx, d/dy, gA, gB, s1, s2
+  static constexpr int WD = 5 + 4 * U + 2 * NR;       // sum ln B, n_bad, d/dx, d/dy, gA, gB, s1, s2, n recomputed
   static constexpr int W = WMC + WD;
   static constexpr int NPL_FULL = Planes<P, S>::W0;    // invariants, width factors, spin factors
   static constexpr int NPL_CACHE = 2 * U;             // component cache (re, im)
@@ -305,7 +305,8 @@ struct Layout {
 };
 
 // Likelihood from the MC column totals `mcs` and the data column totals
-// `ds` of one sample: writes [nll, N, n_bad or status, sum ln B, grad...]
+// `ds` of one sample: writes [nll, N, n_bad or status, sum ln B,
+// n recomputed, grad...]
 // to `res` (and the NLL and gradient to `onll`, `og` when not null).
 //   N = <alpha |A|^2 + beta |Abar|^2 - 2 gc Re(A Abar*) - 2 dc Im(A Abar*)> / Gamma
 // is Eq. (mix) integrated over t in [0, inf) and averaged over the MC sample
@@ -402,6 +403,7 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
       res[1] = N;
       res[2] = nbad;
       res[3] = sum_lnb;
+      res[4] = ds[4 + 4 * U + 2 * NR];
       if (onll) *onll = nll;
       if (trace) trace[6] = global_ns();
     }
@@ -468,7 +470,13 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
   }
 }
 
-template <class P, class S, bool FULL, bool GRAD, bool WEIGHTED>
+// RATES: the variant that writes per-event rates (a.rates); on the fp32
+// path it also recomputes the ill-conditioned data events in double-float,
+// so that every reported rate is within 1e-5 of its double-precision value.
+// Likelihood evaluations without rates keep the fp32 ln B of those few
+// events (their effect on the NLL is orders of magnitude below its 1e-3
+// tolerance) and do not carry the recomputation's code.
+template <class P, class S, bool FULL, bool GRAD, bool WEIGHTED, bool RATES = false>
 __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalArgs a) {
   using T = typename P::T;
   using LY = Layout<P, S>;
@@ -588,7 +596,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
     // ---- data tiles
     {
       double lnb = 0.0;  // sum ln B = lnb + lexp ln 2
-      int bad = 0, lexp = 0;
+      int bad = 0, lexp = 0, n_rec = 0;
       T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
 #pragma unroll
       for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
@@ -608,9 +616,11 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
           const double t_e = reinterpret_cast<const double*>(stage + NPL * TE * ES)[tid];
           const SmemSrc<P, S, TE> src{sbase, tid, false};
           EventCore<P, S> ev;
+          constexpr bool RECOMPUTE = RATES && FULL && P::kF32;
+          T sc[RECOMPUTE ? U : 1];
           if constexpr (FULL) {
             ev.lineshapes(src, bc);
-            ev.components(src);
+            ev.template components<RECOMPUTE>(src, sc);
             T* cache = reinterpret_cast<T*>(static_cast<unsigned char*>(dd.cache) + tile * dd.cache_tile_bytes);
 #pragma unroll
             for (int j = 0; j < U; ++j) {
@@ -626,9 +636,16 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
           }
           T Ar_, Ai_, Br_, Bi_;
           ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
+          double Ad[4] = {double(Ar_), double(Ai_), double(Br_), double(Bi_)};
+          if constexpr (RECOMPUTE) {
+            if (ill_conditioned<U>(bc, sc, Ar_, Ai_, Br_, Bi_, t_e)) {
+              df_amplitudes<S>(sbase, dd.lo + tile * int64_t(S::NX + U * S::NO) * TE, tid, bc, Ad);
+              n_rec += 1;
+            }
+          }
           T tAr, tAi, tBr, tBi;
-          if (mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp, a.rates ? a.rates + i : nullptr,
-                                 tAr, tAi, tBr, tBi, gx, gy)) {
+          if (mix_event<P, GRAD>(bc, logtab, Ad[0], Ad[1], Ad[2], Ad[3], Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp,
+                                 a.rates ? a.rates + i : nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
             if constexpr (GRAD) {
 #pragma unroll
               for (int j = 0; j < U; ++j) {
@@ -645,14 +662,16 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       }
       // block sums of the data accumulators -> rowp[WMC ..]
       {
-        __shared__ int red_bad[kWarps];
+        __shared__ int red_bad[kWarps], red_rec[kWarps];
         const double v0 = warp_sum(fma(double(lexp), kLn2, lnb));
         const int v1 = warp_sum(bad);
+        const int v2 = warp_sum(n_rec);
         if (lane == 0) {
           red_lnb[warp] = v0;
           red_bad[warp] = v1;
+          red_rec[warp] = v2;
         }
-        T vt[WD - 2];
+        T vt[WD - 3];
         vt[0] = gx;
         vt[1] = gy;
 #pragma unroll
@@ -667,16 +686,18 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
           vt[2 + 4 * U + r] = s1[r];
           vt[2 + 4 * U + NR + r] = s2[r];
         }
-        block_sum_df<T, WD - 2>(vt, red, rowp + WMC + 2);  // ends with a barrier
+        block_sum_df<T, WD - 3>(vt, red, rowp + WMC + 2);  // ends with a barrier
         if (tid == 0) {
           double sl = 0;
-          int sb = 0;
+          int sb = 0, sr = 0;
           for (int w = 0; w < kWarps; ++w) {
             sl += red_lnb[w];
             sb += red_bad[w];
+            sr += red_rec[w];
           }
           rowp[WMC] = to_df(sl);
           rowp[WMC + 1] = make_float2(float(sb), 0.f);
+          rowp[WMC + WD - 1] = make_float2(float(sr), 0.f);
         }
       }
     }

@@ -24,7 +24,8 @@ template <bool F32>
 __global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, const DevModel* __restrict__ dm,
                                                     unsigned char* planes, int64_t tile_bytes, int npl,
                                                     const double* __restrict__ t, const double* __restrict__ w,
-                                                    unsigned char* cache, int64_t cache_tile_bytes) {
+                                                    unsigned char* cache, int64_t cache_tile_bytes,
+                                                    float* __restrict__ lo) {
   using T = typename std::conditional<F32, float, double>::type;
   constexpr int TE = kTileEvents;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -64,12 +65,14 @@ __global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, cons
     const double F = barrier(L, q2 * dm->r_res * dm->r_res);
     const double X = qp * F * F / sqrt(s);
     out[(NSP + xp) * TE + e] = T(X);
+    if (F32 && lo) lo[(tile * (NX + NT) + xp) * TE + e] = float(X - double(float(X)));
   }
   for (int k = 0; k < NT; ++k) {
     const int* pt = dm->term_parts[k];
     const double K = spin_barrier(dm->term_spin[k], p[pt[0]], p[pt[1]], p[pt[2]], p[pt[3]], dm->r_res,
                                   dm->r_parent);
     out[(NSP + NX + k) * TE + e] = T(K);
+    if (F32 && lo) lo[(tile * (NX + NT) + NX + k) * TE + e] = float(K - double(float(K)));
   }
   unsigned char* extra = planes + tile * tile_bytes + int64_t(npl) * TE * sizeof(T);
   if (t) {
@@ -82,15 +85,17 @@ __global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, cons
 }
 
 void launch_precompute(bool f32, const Momenta& mom, int64_t n, const DevModel* dm, void* planes, int64_t tile_bytes,
-                       int npl, const double* t, const double* w, void* cache, int64_t cache_tile_bytes,
+                       int npl, const double* t, const double* w, void* cache, int64_t cache_tile_bytes, float* lo,
                        cudaStream_t st) {
   if (n <= 0) return;
   const int threads = 256;
   const unsigned blocks = unsigned((n + threads - 1) / threads);
   auto* pl = static_cast<unsigned char*>(planes);
   auto* ca = static_cast<unsigned char*>(cache);
-  if (f32) k_precompute<true><<<blocks, threads, 0, st>>>(mom, n, dm, pl, tile_bytes, npl, t, w, ca, cache_tile_bytes);
-  else k_precompute<false><<<blocks, threads, 0, st>>>(mom, n, dm, pl, tile_bytes, npl, t, w, ca, cache_tile_bytes);
+  if (f32) k_precompute<true><<<blocks, threads, 0, st>>>(mom, n, dm, pl, tile_bytes, npl, t, w, ca, cache_tile_bytes,
+                                                         lo);
+  else k_precompute<false><<<blocks, threads, 0, st>>>(mom, n, dm, pl, tile_bytes, npl, t, w, ca, cache_tile_bytes,
+                                                          nullptr);
 }
 
 // Fixed-order sum of a vector (one block).

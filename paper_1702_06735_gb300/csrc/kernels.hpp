@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "device_tables.hpp"
 
@@ -15,9 +16,11 @@ struct Momenta {
 
 // Kinematic precompute into the tile-major planes of a sample (see
 // SampleDev); t (data) and w (weighted MC) are device f64 arrays or null;
-// cache (data) receives the decay times of its tiles, or null.
+// cache (data) receives the decay times of its tiles, or null; lo (fp32
+// data) receives the rounding residuals of the width and spin x barrier
+// factors (SampleDev::lo), or null.
 void launch_precompute(bool f32, const Momenta& mom, int64_t n, const DevModel* dm, void* planes, int64_t tile_bytes,
-                       int npl, const double* t, const double* w, void* cache, int64_t cache_tile_bytes,
+                       int npl, const double* t, const double* w, void* cache, int64_t cache_tile_bytes, float* lo,
                        cudaStream_t st);
 void launch_sum(const double* v, int64_t n, double* out, cudaStream_t st);
 
@@ -35,6 +38,9 @@ struct ShapeOps {
   // batched evaluation of serving requests (see serve.cuh)
   cudaError_t (*serve)(bool grad, int grid, cudaStream_t st, const ServeArgs& a);
 };
+
+// Table of the kernels' logarithm ({1/F, ln F} pairs, F = 1 + j/128).
+std::vector<double> make_log_table();
 
 // Specialisation compiled for a model signature, or null.
 const ShapeOps* find_shape_ops(const std::string& signature, bool f32);

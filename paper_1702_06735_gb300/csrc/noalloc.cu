@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads) k_loglik_partials(int U, int64_t n, 
       Br += cbr * ar - cbi * ai;
       Bi += cbr * ai + cbi * ar;
     }
-    // Eq. (mix) as 2 |cosh(w) A - sinh(w) Abar|^2, w = (y + i x) Gamma t / 2
+    // B = 2 |cosh(w) A - sinh(w) Abar|^2, w = (y + i x) gamma t / 2
     const double gt = gamma * t[i];
     const double a = 0.5 * y * gt, b = 0.5 * x * gt;
     double sb, cb;
@@ -116,6 +116,7 @@ extern "C" int tdmix_loglik_components_noalloc(int U, int64_t n, const double* a
   });
   if (g_scratch_err[dev] != cudaSuccess || !g_scratch_addr[dev]) return TDMIX_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();  // a failure left by earlier, unrelated work must not be reported here
   const int64_t want = (n + kThreads - 1) / kThreads;
   const int blocks = int(want < TDMIX_NOALLOC_MAX_BLOCKS ? want : TDMIX_NOALLOC_MAX_BLOCKS);
   k_loglik_partials<<<blocks, kThreads, 0, st>>>(U, n, ld, a_re, a_im, t, cA, cB, x, y, gamma, g_scratch_addr[dev]);

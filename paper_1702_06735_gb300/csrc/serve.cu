@@ -199,14 +199,24 @@ int admit(tdmix_server* s, int id) {
   return TDMIX_OK;
 }
 
+// Device view of a resident sample, copied out of the sample table while
+// the server mutex is held, so that the batch never reads the table (which
+// other threads insert into) without the lock.
+struct ResidentView {
+  const void* cache;
+  int64_t n, tile_bytes;
+  double sum_t;
+};
+
 // Evaluates one batch (worker thread, mutex not held).
-int run_batch(tdmix_server* s, std::vector<Request>& batch, std::vector<Done>& out) {
+int run_batch(tdmix_server* s, std::vector<Request>& batch, const std::vector<ResidentView>& views,
+              std::vector<Done>& out) {
   const ShapeOps* ops = internal::ops_of(s->ctx);
   cudaStream_t st = internal::stream_of(s->ctx);
   const int nb = int(batch.size());
   int chunks = 0;
   for (int r = 0; r < nb; ++r) {
-    SampleRec& rec = s->samples[batch[r].sample];
+    const ResidentView& rec = views[r];
     const int n_tiles = int((rec.n + kTileEvents - 1) / kTileEvents);
     const int ct = std::max(1, (n_tiles + kServeMaxChunks - 1) / kServeMaxChunks);
     ServeReq& q = s->h_reqs[r];
@@ -284,9 +294,15 @@ void worker_loop(tdmix_server* s) {
       s->cv_done.notify_all();
       continue;
     }
+    std::vector<ResidentView> views;
+    views.reserve(batch.size());
+    for (const Request& q : batch) {
+      const SampleRec& rec = s->samples.at(q.sample);
+      views.push_back(ResidentView{rec.cache, rec.n, rec.tile_bytes, rec.sum_t});
+    }
     lk.unlock();
     std::vector<Done> out;
-    int rc = run_batch(s, batch, out);
+    int rc = run_batch(s, batch, views, out);
     lk.lock();
     for (size_t r = 0; r < batch.size(); ++r) {
       Done d = rc ? Done{rc, std::vector<double>(kResHeader + s->np, NAN), now_s() - batch[r].t_submit} : out[r];
@@ -340,7 +356,8 @@ int tdmix_server_create(const char* model_json, int precision, size_t hbm_budget
   SV_CK(cudaMallocHost(&s->h_params, size_t(max_slots) * s->np * sizeof(double)));
   SV_CK(cudaMalloc(&s->d_results, size_t(max_slots) * rw * sizeof(double)));
   SV_CK(cudaMallocHost(&s->h_results, size_t(max_slots) * rw * sizeof(double)));
-  SV_CK(cudaMalloc(&s->d_part, size_t(max_slots) * kServeMaxChunks * wd * 8));
+  // chunk-partial rows with an even stride (16-byte aligned rows, see k_serve)
+  SV_CK(cudaMalloc(&s->d_part, size_t(max_slots) * kServeMaxChunks * ((wd + 1) & ~1) * 8));
   SV_CK(cudaMalloc(&s->d_counters, max_slots * sizeof(unsigned)));
   SV_CK(cudaMemset(s->d_counters, 0, max_slots * sizeof(unsigned)));
   SV_CK(cudaMalloc(&s->d_err, sizeof(int)));

@@ -20,10 +20,14 @@ template <class P, class S>
 struct ServeLayout {
   using T = typename P::T;
   static constexpr int U = S::U, NR = S::NR;
-  static constexpr int WD = 4 + 4 * U + 2 * NR;
+  static constexpr int WD = Layout<P, S>::WD;  // same data columns as the evaluation kernel
+  // row stride of the chunk-partial array: even, so that every row starts on
+  // a 16-byte boundary and a run of rows is a whole number of 16-byte units
+  // (the bulk copy of a request's rows needs both)
+  static constexpr int WR = (WD + 1) & ~1;
   static constexpr int stage_bytes = 2 * U * kTile * int(sizeof(T)) + kTile * 8;
   static constexpr int smem_bytes() {
-    const int st = 2 * stage_bytes, pr = kServeMaxChunks * WD * 8;
+    const int st = 2 * stage_bytes, pr = kServeMaxChunks * WR * 8;
     return st > pr ? st : pr;
   }
 };
@@ -32,7 +36,7 @@ template <class P, class S, bool GRAD>
 __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ ServeArgs a) {
   using T = typename P::T;
   using LY = ServeLayout<P, S>;
-  constexpr int U = S::U, NR = S::NR, WD = LY::WD, TE = kTile, ES = int(sizeof(T));
+  constexpr int U = S::U, NR = S::NR, WD = LY::WD, WR = LY::WR, TE = kTile, ES = int(sizeof(T));
   constexpr int WMC = Layout<P, S>::WMC;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[3];
@@ -116,7 +120,8 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
         T Ar_, Ai_, Br_, Bi_;
         ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
         T tAr, tAi, tBr, tBi;
-        if (mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp, nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
+        if (mix_event<P, GRAD>(bc, logtab, double(Ar_), double(Ai_), double(Br_), double(Bi_), Ar_, Ai_, Br_, Bi_,
+                               t_e, lnb, lexp, nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
           if constexpr (GRAD) {
 #pragma unroll
             for (int k = 0; k < U; ++k) {
@@ -170,8 +175,8 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       rowp[1] = make_float2(float(sb), 0.f);
     }
     __syncthreads();
-    for (int v = tid; v < WD; v += blockDim.x)
-      part[size_t(c) * WD + v] = v < 4 + 4 * U ? rowp[v] : make_float2(0.f, 0.f);
+    for (int v = tid; v < WR; v += blockDim.x)
+      part[size_t(c) * WR + v] = v < 4 + 4 * U ? rowp[v] : make_float2(0.f, 0.f);
     __threadfence();
     __syncthreads();
     if (tid == 0) is_last = atomicAdd(a.counters + r, 1u) == unsigned(q.n_chunks - 1);
@@ -184,9 +189,9 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       asm volatile("fence.proxy.async.global;" ::: "memory");
       mbar_init(&bars[2], 1);
       mbar_fence_init();
-      const uint32_t bytes = uint32_t(q.n_chunks) * uint32_t(WD) * 8u;
+      const uint32_t bytes = uint32_t(q.n_chunks) * uint32_t(WR) * 8u;  // a multiple of 16
       mbar_arrive_expect_tx(&bars[2], bytes);
-      bulk_g2s(sp, part + size_t(q.chunk_begin) * WD, bytes, &bars[2]);
+      bulk_g2s(sp, part + size_t(q.chunk_begin) * WR, bytes, &bars[2]);  // 16-byte aligned
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(&bars[2], 0, kWaitNs);
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
     for (int v = tid; v < WD; v += blockDim.x) {
       float s = 0.f, e = 0.f;
       for (int row = 0; row < q.n_chunks; ++row) {
-        const float2 x = sp[size_t(row) * WD + v];
+        const float2 x = sp[size_t(row) * WR + v];
         float t, er;
         two_sum(s, x.x, t, er);
         s = t;

@@ -34,6 +34,8 @@ _SIGNATURES = {
     "tdmix_default_params": (_c_i, [_c_p, _c_p]),
     "tdmix_set_floating": (_c_i, [_c_p, _c_p]),
     "tdmix_test_withhold_copy": (_c_i, [_c_p, _c_i]),
+    "tdmix_recomputed_events": (_c_i, [_c_p, ctypes.POINTER(ctypes.c_int64)]),
+    "tdmix_test_math": (_c_i, [_c_i, ctypes.c_int64, _c_p, _c_p]),
     "tdmix_load_events": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_nll": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
     "tdmix_event_rates": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
@@ -81,6 +83,24 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         f.argtypes = args
     _lib = lib
     return lib
+
+
+MATH_CODES = {"log_table": 0, "log_cuda": 1, "rcp_f64": 2, "div_f64": 3, "rcp_f32": 4, "div_f32": 5,
+              "df_rcp": 6, "mix_tier0": 7, "mix_tier1": 8, "mix_tier2": 9}
+
+
+def test_math(which: str, v) -> np.ndarray:
+    """Evaluates one of the kernels' math routines (or the CUDA function it
+    replaces) on the device: tdmix_test_math.  Returns n values, or (n, 4)
+    (cosh, sinh, cos, sin) for the mixing-series codes."""
+    lib = load_library()
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    per = 4 if which.startswith("mix") else 1
+    out = np.empty(per * len(a))
+    rc = lib.tdmix_test_math(MATH_CODES[which], len(a), a.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise TDMixError(rc, "tdmix_test_math")
+    return out.reshape(len(a), 4) if per == 4 else out
 
 
 class Events(ctypes.Structure):
@@ -237,6 +257,12 @@ class TDMix:
         out = np.empty(2 * U * U)
         self._check(self._lib.tdmix_norm_matrix(self._ctx, out.ctypes.data))
         return (out[0::2] + 1j * out[1::2]).reshape(U, U)
+
+    def recomputed_events(self) -> int:
+        """Data events the last evaluation recomputed in double-float (fp32 path)."""
+        n = ctypes.c_int64()
+        self._check(self._lib.tdmix_recomputed_events(self._ctx, ctypes.byref(n)))
+        return n.value
 
     def test_withhold_copy(self, enable: bool = True):
         """Test hook: block 0 withholds its first tile copy, so its bounded

@@ -7,14 +7,13 @@ at this size: per-event rates of 20,000 sampled data events (1e-12 of their
 cancellation-free scale) and N over all 10,000,000 MC events in chunks
 (1e-12 relative).  The fp32 precision path is then measured against the fp64
 path on every event and every result; the errors are printed and held to:
-per-event rates 1e-5 relative where the rate is well conditioned (condition
-number, the cancellation-free scale over the rate, below 100; the scale
-counts each Bose ordering of each chain as a separate term, since at
-10,000,000 flat events some events sit where the two orderings of one chain
-nearly cancel) and 1e-6 of the cancellation-free scale for every event (the
-fp32 rounding of the terms, amplified by the cancellation), the NLL per data
-event 2e-8 (the 1e-3-at-50,000-events bar, scaled by the event count), N and
-the normalisation matrix 1e-6 relative to their largest entry, the gradient
+per-event rates 1e-5 relative on every event (ill-conditioned events, whose
+amplitudes nearly cancel between chains or between the two Bose orderings
+of one chain, are recomputed in double-float by the kernel; their number is
+printed) and 1e-6 of the cancellation-free scale (the scale counts each
+Bose ordering of each chain as a separate term), the NLL per data event
+2e-8 (the 1e-3-at-50,000-events bar, scaled by the event count), N and the
+normalisation matrix 1e-6 relative to their largest entry, the gradient
 1e-4 of its largest component.
 
 The data here are flat in phase space with exponential decay times (the
@@ -73,6 +72,7 @@ def test_two_chain_precision_at_ten_million(big):
     # fp32 path against the fp64 path
     c32 = _ctx("d0_k3pi_2chain", "fp32", data, t, mc)
     R32, N32 = c32.event_rates(p)
+    nrec = c32.recomputed_events()
     v32, g32 = c32.nll(p)
     I32 = c32.norm_matrix()
     c32.close()
@@ -81,16 +81,15 @@ def test_two_chain_precision_at_ten_million(big):
     for i in range(0, N_BIG, 1_000_000):
         sl = slice(i, i + 1_000_000)
         cond[sl] = rate_scale_terms(m, data[sl], t[sl], p) / R64[sl]
-    ok = cond < 100
     abs_scaled = np.abs(R32 - R64) / (cond * R64)  # error over the cancellation-free scale
     dI = np.max(np.abs(I32 - I64)) / np.max(np.abs(I64))
     dg = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
-    print(f"\n10M/10M fp32 vs fp64: rate rel err median {np.median(rel):.3e}, max {rel[ok].max():.3e} over the "
-          f"{ok.sum()} events with condition < 100, {np.mean(rel > 1e-5):.2e} of all events above 1e-5; "
+    print(f"\n10M/10M fp32 vs fp64: rate rel err median {np.median(rel):.3e}, max {rel.max():.3e} "
+          f"(condition {cond[rel.argmax()]:.3g}); {nrec} events ({nrec / N_BIG:.2e}) recomputed in double-float; "
           f"max err over the scale {abs_scaled.max():.3e}; "
           f"NLL abs err {abs(v32 - v64):.3e} ({abs(v32 - v64) / N_BIG:.2e} per event); N rel err {abs(N32 / N64 - 1):.3e}; "
           f"I_jk max rel err {dI:.3e}; gradient max err / max |g| {dg:.3e}")
-    assert rel[ok].max() <= 1e-5
+    assert rel.max() <= 1e-5
     assert abs_scaled.max() <= 1e-6
     assert abs(v32 - v64) <= 2e-8 * N_BIG
     assert abs(N32 / N64 - 1) <= 1e-6

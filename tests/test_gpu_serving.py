@@ -9,7 +9,7 @@ import torch
 from conftest import model_path
 from oracle import tdamp
 from paper_1702_06735_gb300 import samples
-from workloads import workload
+from workloads import grad_scale, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +63,8 @@ def test_server_matches_oracle():
                                     floating=mask)
         assert abs(v - v0) <= 1e-12 * abs(v0)
         g0 = g0.numpy()
-        gs = np.maximum(np.abs(g0), 1e-3 * np.abs(g0).max())
-        assert np.max(np.abs(grad - g0) / gs) <= 1e-9
+        S = grad_scale(m, p4, t, mc, p)
+        assert np.max(np.abs(grad - g0) / S) <= 1e-12
     s.close()
 
 

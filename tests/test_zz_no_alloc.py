@@ -62,6 +62,63 @@ def test_noalloc_matches_event_rates_on_two_calls():
     ctx.close()
 
 
+def test_noalloc_many_blocks_and_zero_rates():
+    """n = 300,001 events (more blocks than the scratch array holds, so the
+    grid is clamped and blocks loop over several strides; the finishing pass
+    reads all 1,024 partials) with synthetic components and decay times on
+    the device, against the oracle's factorised rate summed in float64 on
+    the host; then the same call with one component set to zero everywhere
+    and the coefficients of the others zero, so that B = 0 for every event
+    and all of them are counted as bad, on two calls in a row."""
+    from paper_1702_06735_gb300.tdmix import load_library
+    lib = load_library()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    g = np.random.default_rng(99)
+    n, U, ld = 300_001, 5, 300_016
+    are = g.normal(size=(U, n))
+    aim = g.normal(size=(U, n))
+    t = g.exponential(0.41, n)
+    cA = g.normal(size=2 * U)
+    cB = g.normal(size=2 * U)
+    x, y, gamma = 0.0049, 0.0061, 1.0 / 0.4101
+    a = torch.complex(torch.from_numpy(are), torch.from_numpy(aim))
+    A = (torch.complex(torch.from_numpy(cA[0::2]), torch.from_numpy(cA[1::2]))[:, None] * a).sum(0)
+    Ab = (torch.complex(torch.from_numpy(cB[0::2]), torch.from_numpy(cB[1::2]))[:, None] * a).sum(0)
+    _, B = tdamp.rate_factorised(A, Ab, torch.from_numpy(t), x, y, gamma)
+    want = float(torch.log(B).sum())
+    d_re = torch.zeros(U, ld, dtype=F64, device=dev)
+    d_im = torch.zeros(U, ld, dtype=F64, device=dev)
+    d_re[:, :n] = torch.from_numpy(are).to(dev)
+    d_im[:, :n] = torch.from_numpy(aim).to(dev)
+    d_t = torch.from_numpy(t).to(dev)
+    d_cA = torch.from_numpy(cA).to(dev)
+    d_cB = torch.from_numpy(cB).to(dev)
+    out = torch.full((2,), float("nan"), dtype=F64, device=dev)
+    for _ in range(2):
+        rc = lib.tdmix_loglik_components_noalloc(U, n, d_re.data_ptr(), d_im.data_ptr(), ld, d_t.data_ptr(),
+                                                 d_cA.data_ptr(), d_cB.data_ptr(), x, y, gamma, out.data_ptr(),
+                                                 stream)
+        assert rc == 0
+        torch.cuda.synchronize(dev)
+        got = out.cpu().numpy()
+        assert got[1] == 0
+        assert abs(got[0] - want) <= 1e-12 * float(torch.log(B).abs().sum())
+    # B = 0 everywhere: component 0 is zero and only it has nonzero coefficients
+    d_re[0].zero_()
+    d_im[0].zero_()
+    zc = torch.zeros(2 * U, dtype=F64, device=dev)
+    zc[0:2] = 1.0
+    for _ in range(2):
+        out.fill_(float("nan"))
+        rc = lib.tdmix_loglik_components_noalloc(U, n, d_re.data_ptr(), d_im.data_ptr(), ld, d_t.data_ptr(),
+                                                 zc.data_ptr(), zc.data_ptr(), x, y, gamma, out.data_ptr(), stream)
+        assert rc == 0
+        torch.cuda.synchronize(dev)
+        got = out.cpu().numpy()
+        assert got[1] == n and got[0] == 0.0
+
+
 def test_noalloc_rejects_out_of_range_sizes():
     from paper_1702_06735_gb300.tdmix import load_library
     lib = load_library()

@@ -83,3 +83,29 @@ def rate_scale_terms(model, data, t, params):
     gt = model.gamma * torch.as_tensor(t)
     return (2 * torch.exp(-gt) * torch.cosh(y * gt) * s ** 2).numpy()
 
+
+
+def grad_scale(model, data, t, mc, params, mc_weights=None):
+    """Cancellation-free scale of each NLL gradient component:
+    S_k = sum_e |d ln R_e / d theta_k| + N_d sum_m w_m |d f_m / d theta_k| / sum_m w_m f_m,
+    with R_e the data rates and f_m the time-integrated rate of MC event m
+    (NLL = -sum ln R_e + N_d ln N, N = <f>).  Rounding errors of a gradient
+    formed from these terms scale with S_k, not with |g_k|, which can be
+    near zero by cancellation between the data and normalisation parts.
+    Forward-mode Jacobians through the oracle."""
+    p = torch.as_tensor(params, dtype=torch.float64)
+    d = torch.as_tensor(data, dtype=torch.float64)
+    tt = torch.as_tensor(t, dtype=torch.float64)
+    mm = torch.as_tensor(mc, dtype=torch.float64)
+    Jd = torch.func.jacfwd(lambda q: torch.log(tdamp.event_rates(model, d, tt, q)))(p)
+
+    def f_mc(q):
+        _, _, _, x, y = tdamp._unpack(model, q)
+        A, Ab = tdamp.amplitudes(model, mm, q)
+        return tdamp.norm_integrand(A, Ab, x, y, model.gamma)
+    with torch.no_grad():
+        f = f_mc(p)
+    Jm = torch.func.jacfwd(f_mc)(p)
+    w = torch.ones(len(mm), dtype=torch.float64) if mc_weights is None else torch.as_tensor(mc_weights)
+    S = Jd.abs().sum(0) + len(d) * (w[:, None] * Jm.abs()).sum(0) / (w * f).sum()
+    return S.numpy()
