@@ -151,6 +151,23 @@ int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, d
  * (re, im) pairs, row-major in (j, k). */
 int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
 
+/* How the MC normalisation matrix I_jk (Sec. 3.1) is accumulated:
+ *   TDMIX_GRAM_AUTO       (default) per-thread register accumulation up to 8
+ *                         shared components; beyond that the tensor cores
+ *                         (fp32 path) or shared-memory sums (fp64 path);
+ *   TDMIX_GRAM_REGISTERS  per-thread register accumulation (up to 8
+ *                         components);
+ *   TDMIX_GRAM_TENSOR     tcgen05 tensor-core MMAs over each 256-event MC
+ *                         tile on exact fixed-point pieces (three bf16
+ *                         integer pieces per value, exact integer sums in the
+ *                         MMA, double-float accumulation across tiles; fp32
+ *                         path only).
+ * Returns TDMIX_ERR_UNSUPPORTED for a mode the context's precision or model
+ * cannot use, TDMIX_ERR_ARG for an unknown mode.  Results agree between
+ * modes within the fp32 path's tolerance (the modes round differently). */
+enum { TDMIX_GRAM_AUTO = 0, TDMIX_GRAM_REGISTERS = 1, TDMIX_GRAM_TENSOR = 2 };
+int tdmix_set_gram(tdmix_ctx* ctx, int mode);
+
 /* Number of data events the last evaluation recomputed in double-float
  * (fp32 precision path only; 0 on the fp64 path).  The fp32 amplitudes
  * carry rounding errors of a few ulps of the magnitude of their terms (the

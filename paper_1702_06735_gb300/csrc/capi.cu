@@ -64,6 +64,7 @@ struct tdmix_ctx {
   std::vector<double> last_res;
   bool cache_valid = false, gram_valid = false;
   bool withhold_first_copy = false;  // test hook (tdmix_test_withhold_copy)
+  int gram_pref = TDMIX_GRAM_AUTO;   // normalisation-matrix accumulation (tdmix_set_gram)
   std::string err;
   // kernel profiling: CUDA event pairs per kernel class, recorded on the stream
   bool prof_on = false;
@@ -392,6 +393,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.out_grad = out_grad;
   a.logtab = ctx->d_logtab;
   a.withhold_first_copy = ctx->withhold_first_copy ? 1 : 0;
+  a.gram_pref = ctx->gram_pref;
   a.sum_t = ctx->sum_t;
   a.inv_sum_w = ctx->inv_sum_w;
   a.trace = ctx->d_trace;
@@ -702,6 +704,21 @@ int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, in
       ctx->prof_n[c] = 0;
     }
   }
+  return TDMIX_OK;
+}
+
+int tdmix_set_gram(tdmix_ctx* ctx, int mode) {
+  if (!ctx) return TDMIX_ERR_ARG;
+  if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  if (mode != TDMIX_GRAM_AUTO && mode != TDMIX_GRAM_REGISTERS && mode != TDMIX_GRAM_TENSOR)
+    return fail(ctx, TDMIX_ERR_ARG, "unknown normalisation-matrix mode");
+  if (mode == TDMIX_GRAM_TENSOR && !ctx->f32)
+    return fail(ctx, TDMIX_ERR_UNSUPPORTED, "the tensor-core normalisation matrix runs on the fp32 path");
+  if (mode == TDMIX_GRAM_REGISTERS && ctx->model.U > 8)
+    return fail(ctx, TDMIX_ERR_UNSUPPORTED, "register accumulation of the normalisation matrix holds up to 8 components");
+  ctx->gram_pref = mode;
+  ctx->gram_valid = false;  // the stored normalisation sums came from the other mode
+  ctx->cache_valid = false;
   return TDMIX_OK;
 }
 

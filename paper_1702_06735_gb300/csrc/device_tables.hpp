@@ -86,6 +86,7 @@ struct EvalArgs {
   const void* logtab;         // logarithm table: double2 {1/F, ln F}, F = 1 + j/128, j = 0..128
   int withhold_first_copy;    // test hook: block 0 does not issue its first tile copy, so its
                               // bounded wait for that tile runs out (TDMIX_ERR_TIMEOUT)
+  int gram_pref;              // how to accumulate the MC normalisation matrix (TDMIX_GRAM_*)
 };
 
 // Phases stamped by the evaluation kernel when tracing is on: start,

@@ -7,6 +7,7 @@
 #include "serve.cuh"
 #include "kernels.hpp"
 #include "shapes_gen.h"
+#include "../../include/tdmix.h"
 
 #ifndef TDMIX_PREC_F32
 #error "define TDMIX_PREC_F32"
@@ -57,26 +58,46 @@ cudaError_t allow_smem(F* f, int smem, SmemLimit& lim) {
 
 template <class S>
 struct Ops {
-  static constexpr bool kOk = S::U <= kMaxRegisterGramU;
-  template <bool FULL, bool GRAD, bool W, bool RATES = false>
+  // normalisation-matrix accumulation available for this structure
+  static constexpr bool kRegs = S::U <= kMaxRegisterGramU;
+  static constexpr bool kTensor = Prec::kF32 && S::U <= 16;
+  static constexpr bool kShared = !Prec::kF32 && !kRegs && S::U <= 16;
+  static constexpr bool kOk = kRegs || kTensor || kShared;
+  // the mode of the cached path (no MC tiles: the mode only names the kernel)
+  static constexpr int kCacheGram = kRegs ? kGramRegs : (Prec::kF32 ? kGramTensor : kGramShared);
+
+  template <bool FULL, bool GRAD, bool W, bool RATES, int GRAM>
   static cudaError_t launch(int grid, cudaStream_t st, const EvalArgs& a) {
-    const int smem = Layout<Prec, S>::smem_bytes(FULL, int(a.ld));
+    const int smem = Layout<Prec, S, GRAM>::smem_bytes(FULL, int(a.ld));
     static SmemLimit seen;  // per instantiation
-    const cudaError_t e = allow_smem(k_eval<Prec, S, FULL, GRAD, W, RATES>, smem, seen);
+    const cudaError_t e = allow_smem(k_eval<Prec, S, FULL, GRAD, W, RATES, GRAM>, smem, seen);
     if (e != cudaSuccess) return e;
-    k_eval<Prec, S, FULL, GRAD, W, RATES><<<grid, kTile, smem, st>>>(a);
+    k_eval<Prec, S, FULL, GRAD, W, RATES, GRAM><<<grid, kTile, smem, st>>>(a);
     return cudaGetLastError();
+  }
+  template <int GRAM>
+  static cudaError_t eval_full(bool grad, int grid, cudaStream_t st, const EvalArgs& a) {
+    const bool w = a.mc.weighted != 0;
+    if (a.rates && !grad)  // per-event rates (always a full evaluation without gradient)
+      return w ? launch<true, false, true, true, GRAM>(grid, st, a) : launch<true, false, false, true, GRAM>(grid, st, a);
+    if (grad)
+      return w ? launch<true, true, true, false, GRAM>(grid, st, a) : launch<true, true, false, false, GRAM>(grid, st, a);
+    return w ? launch<true, false, true, false, GRAM>(grid, st, a) : launch<true, false, false, false, GRAM>(grid, st, a);
   }
   static cudaError_t eval(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a) {
     if constexpr (kOk) {
-      const bool w = a.mc.weighted != 0;
-      if (a.rates && full && !grad)  // per-event rates (always a full evaluation without gradient)
-        return w ? launch<true, false, true, true>(grid, st, a) : launch<true, false, false, true>(grid, st, a);
-      if (full) {
-        if (grad) return w ? launch<true, true, true>(grid, st, a) : launch<true, true, false>(grid, st, a);
-        return w ? launch<true, false, true>(grid, st, a) : launch<true, false, false>(grid, st, a);
+      if (!full)
+        return grad ? launch<false, true, false, false, kCacheGram>(grid, st, a)
+                    : launch<false, false, false, false, kCacheGram>(grid, st, a);
+      if constexpr (Prec::kF32) {
+        if constexpr (kRegs)
+          if (a.gram_pref != TDMIX_GRAM_TENSOR) return eval_full<kGramRegs>(grad, grid, st, a);
+        return eval_full<kGramTensor>(grad, grid, st, a);
+      } else {
+        if (a.gram_pref == TDMIX_GRAM_TENSOR) return cudaErrorNotSupported;
+        if constexpr (kRegs) return eval_full<kGramRegs>(grad, grid, st, a);
+        else return eval_full<kGramShared>(grad, grid, st, a);
       }
-      return grad ? launch<false, true, false>(grid, st, a) : launch<false, false, false>(grid, st, a);
     }
     return cudaErrorNotSupported;
   }

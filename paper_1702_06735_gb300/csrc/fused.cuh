@@ -26,9 +26,21 @@
 #include "async_copy.cuh"
 #include "device_tables.hpp"
 #include "eval.cuh"
+#include "gram_tc.cuh"
 #include "kinematics.cuh"
 
 namespace tdmix {
+
+// How a block accumulates the MC normalisation matrix over its tiles:
+//   kGramRegs    per-thread register accumulators of every entry (up to 8
+//                shared components), block sums at the end;
+//   kGramTensor  tcgen05 MMAs per tile on exact fixed-point pieces,
+//                folded into double-float accumulators (fp32 path, any
+//                supported U; see gram_tc.cuh);
+//   kGramShared  per tile the components are written to shared memory and
+//                thread q sums the q-th entry over the tile's events (fp64
+//                path beyond 8 components).
+enum GramMode { kGramRegs = 0, kGramTensor = 1, kGramShared = 2 };
 
 constexpr int kTile = kTileEvents;
 constexpr int kWarps = kTile / 32;
@@ -269,7 +281,7 @@ __device__ inline void block_sum_df(const T (&vt)[NQ], T* red, float2* out) {
   __syncthreads();
 }
 
-template <class P, class S>
+template <class P, class S, int GRAM = kGramRegs>
 struct Layout {
   using T = typename P::T;
   static constexpr int U = S::U, NR = S::NR;
@@ -284,10 +296,14 @@ struct Layout {
   static constexpr int stage_bytes(bool full) {
     return (full ? NPL_FULL : NPL_CACHE) * kTile * int(sizeof(T)) + kTile * 8;
   }
+  // shared memory after the ring used by the tensor-core normalisation matrix
+  static constexpr int extra_bytes(bool full) {
+    return (full && GRAM == kGramTensor) ? TcGram<U>::extra_bytes : 0;
+  }
   // ring depth: as many stages as fit the budget, 2 to 6 (the lookahead must
   // cover the memory latency under full load, a few microseconds)
   static constexpr int stages(bool full) {
-    const int n = kStageBudget / stage_bytes(full);
+    const int n = (kStageBudget - extra_bytes(full)) / stage_bytes(full);
     return n < 2 ? 2 : (n > 6 ? 6 : n);
   }
   // bytes of one tile in global memory (SampleDev::tile_bytes / cache_tile_bytes)
@@ -296,10 +312,17 @@ struct Layout {
     return int64_t(NPL_FULL) * kTile * sizeof(T) + (weighted ? kTile * sizeof(T) : 0);
   }
   static constexpr int64_t cache_tile_bytes() { return int64_t(NPL_CACHE) * kTile * sizeof(T) + kTile * 8; }
-  // dynamic shared memory: the stage ring, reused by the last block for the
-  // partial rows of up to `ld` blocks (copied in whole 16-byte units)
+  // the last block copies the partial rows of `g` blocks into shared memory
+  // (whole 16-byte units) when they fit; otherwise it reads them from global
+  // memory (L2)
+  static constexpr int partial_bytes(int g) { return W * g * 8 + 16; }
+  static constexpr bool partials_in_smem(int g) { return partial_bytes(g) <= kStageBudget; }
+  // dynamic shared memory: the stage ring and the normalisation-matrix
+  // buffers, reused by the last block for the partial rows of up to `ld`
+  // blocks
   static constexpr int smem_bytes(bool full, int ld) {
-    const int st = stages(full) * stage_bytes(full), pa = W * ld * 8 + 16;
+    const int st = stages(full) * stage_bytes(full) + extra_bytes(full);
+    const int pa = partials_in_smem(ld) ? partial_bytes(ld) : 0;
     return st > pa ? st : pa;
   }
 };
@@ -476,10 +499,15 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
 // Likelihood evaluations without rates keep the fp32 ln B of those few
 // events (their effect on the NLL is orders of magnitude below its 1e-3
 // tolerance) and do not carry the recomputation's code.
-template <class P, class S, bool FULL, bool GRAD, bool WEIGHTED, bool RATES = false>
+// GRAM: how the MC normalisation matrix is accumulated (GramMode).
+template <class P, class S, bool FULL, bool GRAD, bool WEIGHTED, bool RATES = false, int GRAM = kGramRegs>
 __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalArgs a) {
   using T = typename P::T;
-  using LY = Layout<P, S>;
+  using LY = Layout<P, S, GRAM>;
+  static_assert(GRAM != kGramTensor || P::kF32, "tensor-core normalisation matrix on the fp32 path");
+  static_assert(GRAM != kGramRegs || S::U <= 8, "register accumulation of the normalisation matrix up to 8 components");
+  constexpr bool TCG = FULL && GRAM == kGramTensor;
+  constexpr bool SMG = FULL && GRAM == kGramShared;
   constexpr int U = S::U, NR = S::NR, NRE = LY::NRE, NIM = LY::NIM, WMC = LY::WMC, WD = LY::WD;
   constexpr int NPL = FULL ? LY::NPL_FULL : LY::NPL_CACHE;
   constexpr int NST = LY::stages(FULL);
@@ -493,12 +521,19 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   __shared__ unsigned s_issued;       // items whose copy has been issued
   __shared__ CtaConst cc;
   __shared__ BlockConst<T> bc;
-  __shared__ T red[kWarps * (WMC > WD ? WMC : WD)];
+  constexpr int RED_MC = GRAM == kGramRegs ? WMC : 1 + 2 * NR;  // per-thread MC columns summed over the block
+  __shared__ T red[kWarps * (RED_MC > WD ? RED_MC : WD)];
   __shared__ double red_lnb[kWarps];
   __shared__ float2 rowp[LY::W];   // this block's partial row (double-float)
   __shared__ double colsum[LY::W];
   __shared__ unsigned s_last, s_timeout;
   __shared__ double2 logtab[kLogTable];
+  // tensor-core normalisation matrix: MMA completion, TMEM base, column
+  // exponents of the last three tiles (written, read, being reset)
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ unsigned s_E[3][TCG ? TcGram<U>::CP : 1];
+  __shared__ float2 mc_small[1 + 2 * kMaxRes];  // block sums of the MC weight and lineshape sensitivities
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
@@ -545,17 +580,32 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       released[s] = 0;
     }
     mbar_init(&part_bar, 1);
+    if constexpr (TCG) mbar_init(&mma_bar, 1);
     mbar_fence_init();
     // the first tile does not depend on the parameters (the test hook
     // withholds block 0's, so that its bounded wait runs out)
     if (my_items > 0 && !(a.withhold_first_copy && b == 0)) issue(0);
+  }
+  // tensor-core normalisation matrix: TMEM for the accumulator (warp 0),
+  // zeroed operand buffer and accumulators, per-tile column exponents
+  const TcGramSmem<U> tg = TcGramSmem<U>::at(smem_raw + NST * STB);
+  if constexpr (TCG) {
+    if (warp == 0) tmem_alloc(&s_tmem, TcGram<U>::TMEM_COLS);
+    tg.init();
+    for (int v = tid; v < 3 * TcGram<U>::CP; v += kTile) (&s_E[0][0])[v] = 0u;
   }
   if (!FULL)  // stored MC totals of the fixed lineshapes
     for (int v = tid; v < WMC; v += kTile) colsum[v] = a.gram_store[v];
   for (int j = tid; j < kLogTable; j += kTile) logtab[j] = static_cast<const double2*>(a.logtab)[j];
   // the parameter loads go out before the other tile copies flood the memory system
   derive_load<T, U>(a.params, a.hp, a.km, cc, bc);
+  if constexpr (TCG) tc_fence_before_sync();
   __syncthreads();
+  uint32_t tmem = 0;
+  if constexpr (TCG) {
+    tc_fence_after_sync();
+    tmem = s_tmem;
+  }
   if (tid == 0) {
     const int64_t first = my_items < NST ? my_items : NST;
     for (int64_t k = 1; k < first; ++k) issue(k);
@@ -704,7 +754,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
     if (trace && tid == 0) trace[2] = global_ns();
 
     // ---- MC tiles
-    if constexpr (FULL) {
+    if constexpr (FULL && GRAM == kGramRegs) {
       T sw = 0, gre[NRE], gim[NIM > 0 ? NIM : 1], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
 #pragma unroll
       for (int q = 0; q < NRE; ++q) gre[q] = 0;
@@ -774,9 +824,163 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       }
       block_sum_df<T, WMC>(vt, red, rowp);
     }
+    if constexpr (TCG || SMG) {
+      // Block-synchronous tiles: every thread takes part in every barrier,
+      // and a bounded wait that gives up stops all of them.
+      using TG = TcGram<U>;
+      constexpr int CPX = TCG ? TG::CP : 1;
+      if constexpr (SMG) static_assert(2 * U * TE * 8 <= STB, "the components of a tile fit its stage");
+      timed_out = __syncthreads_or(timed_out) != 0;
+      T sw = 0, s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
+#pragma unroll
+      for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
+      // kGramShared: this thread's entry of the normalisation sums, Re over
+      // j <= k for q < NRE, Im over j < k after that (row-major)
+      double gacc = 0.0;
+      int gj = 0, gk = 0;
+      const bool g_re = tid < NRE;
+      if constexpr (SMG) {
+        int r = g_re ? tid : tid - NRE;
+        for (;;) {
+          const int len = g_re ? U - gj : U - 1 - gj;
+          if (r < len || gj >= U) break;
+          r -= len;
+          ++gj;
+        }
+        gk = g_re ? gj + r : gj + 1 + r;
+      }
+      int t3 = 0;
+      uint32_t mma_phase = 0;
+      bool mma_in_flight = false;
+      for (; k < my_items && !timed_out; ++k) {
+        const int64_t tile = mc_begin + (k - my_data);
+        const bool ok = mbar_wait_bounded(&full_bar[st], ph, kWaitNs);
+        const int64_t i = tile * TE + tid;
+        const bool valid = ok && i < dmc.n;
+        unsigned char* stage = smem_raw + st * STB;
+        const T* sbase = reinterpret_cast<const T*>(stage);
+        const SmemSrc<P, S, TE> src{sbase, tid, false};
+        EventCore<P, S> ev;
+        T w = T(0);
+        if (valid) {
+          ev.lineshapes(src, bc);
+          ev.components(src);
+          w = WEIGHTED ? reinterpret_cast<const T*>(stage + NPL * TE * ES)[tid] : T(1);
+          sw += w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < U; ++j) ev.ar[j] = ev.ai[j] = T(0);
+        }
+        const T sq = WEIGHTED ? sqrt(w) : T(1);  // G = X^T X with sqrt(w) in each row
+        // the adjoint of the time-integrated rate (needs this tile's planes)
+        auto adjoint = [&]() {
+          if constexpr (GRAD) {
+            if (valid) {
+              T Ar, Ai, Br, Bi;
+              ev.amplitudes(bc, Ar, Ai, Br, Bi);
+              const Quad<T> M = bc.mix;  // {alpha, beta, gc, dc}, see the register variant
+              const T uAr = M.x * Ar - M.z * Br + M.w * Bi;
+              const T uAi = -M.x * Ai + M.z * Bi + M.w * Br;
+              const T uBr = M.y * Br - M.z * Ar - M.w * Ai;
+              const T uBi = -M.y * Bi + M.z * Ai - M.w * Ar;
+              ev.template backprop_lineshapes<WEIGHTED>(src, bc, uAr, uAi, uBr, uBi, w, s1, s2);
+            }
+          }
+        };
+        if constexpr (TCG) {
+          float x[CPX];
+#pragma unroll
+          for (int c = 0; c < CPX; ++c) x[c] = 0.f;
+#pragma unroll
+          for (int j = 0; j < U; ++j) {
+            x[j] = float(ev.ar[j] * sq);
+            x[U + j] = float(ev.ai[j] * sq);
+          }
+          // largest exponent of each column over the tile
+          unsigned mine = 0;
+#pragma unroll
+          for (int c = 0; c < CPX; ++c) {
+            const unsigned e = __reduce_max_sync(0xffffffffu, exp_bits(x[c]));
+            if (lane == c) mine = e;
+          }
+          if (lane < CPX) atomicMax(&s_E[t3][lane], mine < 7u ? 7u : mine);
+          if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+          }
+          if (tid < CPX) s_E[t3 == 0 ? 2 : t3 - 1][tid] = 0u;  // buffer of tile k + 2
+          tg.store_pieces(x, s_E[t3], tid);
+          __syncthreads();
+          if (tid == 0) tg.issue(tmem, &mma_bar);
+          mma_in_flight = true;
+          adjoint();
+          const bool ok2 = mbar_wait_bounded(&mma_bar, mma_phase, kWaitNs);
+          mma_phase ^= 1u;
+          tc_fence_after_sync();
+          if (ok2) mma_in_flight = false;
+          tg.stage(tmem);
+          tc_fence_before_sync();
+          if (__syncthreads_or(!ok2)) {
+            timed_out = true;
+            break;
+          }
+          tg.fold(s_E[t3]);
+          t3 = t3 == 2 ? 0 : t3 + 1;
+        } else {
+          adjoint();
+          if (__syncthreads_or(!ok)) {  // every thread is done with the planes
+            timed_out = true;
+            break;
+          }
+          T* X = reinterpret_cast<T*>(stage);  // [2U][256] components, re then im
+#pragma unroll
+          for (int j = 0; j < U; ++j) {
+            X[j * TE + tid] = ev.ar[j] * sq;
+            X[(U + j) * TE + tid] = ev.ai[j] * sq;
+          }
+          __syncthreads();
+          if (tid < NRE + NIM) {
+            const T* xj = X + gj * TE;
+            const T* xk = X + gk * TE;
+            const T* yj = X + (U + gj) * TE;
+            const T* yk = X + (U + gk) * TE;
+            // lanes start at different events (no shared-memory bank conflicts)
+            for (int e0 = 0; e0 < TE; ++e0) {
+              const int e = (e0 + lane) & (TE - 1);
+              gacc = g_re ? fma(xj[e], xk[e], fma(yj[e], yk[e], gacc)) : fma(xj[e], yk[e], fma(-yj[e], xk[e], gacc));
+            }
+          }
+          __syncthreads();  // before the stage is refilled
+        }
+        release();
+      }
+      if constexpr (TCG) {
+        if (mma_in_flight && tid == 0)  // a wait gave up: let the MMA finish before TMEM is freed
+          mbar_wait_bounded(&mma_bar, mma_phase ^ 1u, kWaitNs);
+      }
+      T vt[1 + 2 * NR];
+      vt[0] = sw;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        vt[1 + r] = s1[r];
+        vt[1 + NR + r] = s2[r];
+      }
+      block_sum_df<T, 1 + 2 * NR>(vt, red, mc_small);  // ends with a barrier
+      for (int v = tid; v < 1 + 2 * NR; v += blockDim.x) rowp[v == 0 ? 0 : NRE + NIM + v] = mc_small[v];
+      if constexpr (TCG) tg.finish(rowp + 1, rowp + 1 + NRE);
+      if constexpr (SMG)
+        if (tid < NRE + NIM) rowp[1 + tid] = to_df(gacc);
+    }
     if (trace && tid == 0) trace[3] = global_ns();
   }
+  if constexpr (TCG) tc_fence_before_sync();
   const int block_timed_out = __syncthreads_or(timed_out);
+  if constexpr (TCG) {
+    if (warp == 0) {
+      tc_fence_after_sync();
+      tmem_dealloc(tmem, TcGram<U>::TMEM_COLS);
+    }
+  }
   if (block_timed_out && tid == 0) {
     // copies no warp waited for (the last one of each stage) land before
     // shared memory is reused or released
@@ -806,21 +1010,25 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   }
   {
     // The partial rows of all blocks ([G][W] double-float pairs) come into
-    // shared memory (the idle stage ring) by one bulk copy.  Thread
-    // (column c, half h) sums the rows of its half in order with TwoSum,
-    // lanes on consecutive columns (no bank conflicts); the halves are
-    // combined through shared memory.
+    // shared memory (the idle stage ring) by one bulk copy when they fit,
+    // else they are read from global memory (L2).  Thread (column c, half h)
+    // sums the rows of its half in order with TwoSum, lanes on consecutive
+    // columns (no bank conflicts); the halves are combined through shared
+    // memory.
     constexpr int HC = kTile / 2;
     __shared__ float2 half_sum[HC];
-    float2* sp = reinterpret_cast<float2*>(smem_raw);
-    if (tid == 0) {
-      asm volatile("fence.proxy.async;" ::: "memory");
-      const uint32_t bytes = (uint32_t(G) * uint32_t(LY::W) * 8u + 15u) & ~15u;
-      mbar_arrive_expect_tx(&part_bar, bytes);
-      bulk_g2s(sp, part, bytes, &part_bar);
+    const bool parts_smem = LY::partials_in_smem(G);
+    const float2* sp = parts_smem ? reinterpret_cast<const float2*>(smem_raw) : part;
+    if (parts_smem) {
+      if (tid == 0) {
+        asm volatile("fence.proxy.async;" ::: "memory");
+        const uint32_t bytes = (uint32_t(G) * uint32_t(LY::W) * 8u + 15u) & ~15u;
+        mbar_arrive_expect_tx(&part_bar, bytes);
+        bulk_g2s(smem_raw, part, bytes, &part_bar);
+      }
+      const bool ok = mbar_wait_bounded(&part_bar, 0, kWaitNs);
+      if (__syncthreads_or(!ok) && tid == 0) s_timeout += 1u;
     }
-    const bool ok = mbar_wait_bounded(&part_bar, 0, kWaitNs);
-    if (__syncthreads_or(!ok) && tid == 0) s_timeout += 1u;
     const int c0 = FULL ? 0 : WMC;
     const int ncol = LY::W - c0;
     const int half_rows = (G + 1) / 2;

@@ -35,6 +35,7 @@ _SIGNATURES = {
     "tdmix_set_floating": (_c_i, [_c_p, _c_p]),
     "tdmix_test_withhold_copy": (_c_i, [_c_p, _c_i]),
     "tdmix_recomputed_events": (_c_i, [_c_p, ctypes.POINTER(ctypes.c_int64)]),
+    "tdmix_set_gram": (_c_i, [_c_p, _c_i]),
     "tdmix_test_math": (_c_i, [_c_i, ctypes.c_int64, _c_p, _c_p]),
     "tdmix_load_events": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_nll": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
@@ -257,6 +258,13 @@ class TDMix:
         out = np.empty(2 * U * U)
         self._check(self._lib.tdmix_norm_matrix(self._ctx, out.ctypes.data))
         return (out[0::2] + 1j * out[1::2]).reshape(U, U)
+
+    GRAM_MODES = {"auto": 0, "registers": 1, "tensor": 2}
+
+    def set_gram(self, mode: str):
+        """Accumulation of the MC normalisation matrix: "auto", "registers" or
+        "tensor" (tcgen05 tensor cores, fp32 path)."""
+        self._check(self._lib.tdmix_set_gram(self._ctx, self.GRAM_MODES[mode]))
 
     def recomputed_events(self) -> int:
         """Data events the last evaluation recomputed in double-float (fp32 path)."""

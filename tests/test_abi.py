@@ -71,11 +71,18 @@ def test_null_arguments(lib):
 
 
 def test_model_beyond_the_compiled_specialisations_is_refused(lib):
-    """16 components (the full model without shared blocks) exceed the
-    register-Gram limit of the compiled library: creation reports TDMIX_ERR_UNSUPPORTED
-    (before any device call) with a message, instead of a slower path."""
+    """A structure none of the shipped model files has (the 2-chain model
+    plus a D-wave K*0 rho0 chain) is not compiled into the library: creation
+    reports TDMIX_ERR_UNSUPPORTED (before any device call) with a message."""
+    import copy
+    import json
+    from conftest import model_path
     from paper_1702_06735_gb300.tdmix import TDMix, TDMixError
+    d = json.load(open(model_path("d0_k3pi_2chain")))
+    extra = copy.deepcopy(d["chains"][0])
+    extra.update(name="CF K*0 rho0 D-wave", spin="VV_D", coef=[0.3, 0.1], float=True)
+    d["chains"].append(extra)
     with pytest.raises(TDMixError) as e:
-        TDMix("d0_k3pi_full_nodedup", "fp32")
+        TDMix(d, "fp32")
     assert e.value.code == -8
     assert "not compiled" in str(e.value)
