@@ -151,6 +151,35 @@ int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, d
  * (re, im) pairs, row-major in (j, k). */
 int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
 
+/* Pseudo-events of the context's model on the GPU (Sec. 3.1: flat
+ * phase-space points and time-dependent pseudo-events by accept/reject).
+ * Candidates are flat four-body phase-space points (GENBOD, F. James, CERN
+ * 68-15) with decay times t ~ Exp((1 - |y|) Gamma); with flat == 0 each is
+ * kept with probability R e^{(1-|y|) Gamma t} / env, R = e^{-Gamma t} B the
+ * rate of Eq. (mix) at `params` (double precision, whatever the context's
+ * precision), env 1.5 times the largest weight of a pilot batch (raised
+ * and the sample redrawn, at most four times, if a later weight exceeds
+ * it); with flat != 0 every phase-space point is kept and t is 0.  Random
+ * numbers: Philox4x32-10 (Salmon et al., SC'11) with key `seed`, counter
+ * (candidate index, stream, draw), so the sample depends only on (seed,
+ * stream, params, n) and is written in candidate order.
+ *   params  host, num_params doubles (ignored when flat)
+ *   p_out   device, 16 planes of n doubles: component c (E, px, py, pz) of
+ *           final-state particle a at p_out[(4a + c) n + i] (the layout of
+ *           tdmix_events with on_device = 1)
+ *   t_out   device, n decay times (ps), or NULL
+ *   info    host, 4 doubles or NULL: envelope, candidates drawn, accepted
+ *           fraction, envelope raises
+ * Synchronises with the context's stream; allocates temporary device
+ * buffers.  TDMIX_ERR_NONFINITE if the pilot finds no positive finite rate
+ * or the envelope keeps being exceeded. */
+int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t seed, uint32_t stream, int flat,
+                   double* p_out, double* t_out, double* info);
+
+/* Philox4x32-10 of the generator for one (counter, key) (self-test entry;
+ * the paper has no counterpart): out receives the four 32-bit words. */
+int tdmix_test_philox(const uint32_t* counter, const uint32_t* key, uint32_t* out);
+
 /* How the MC normalisation matrix I_jk (Sec. 3.1) is accumulated:
  *   TDMIX_GRAM_AUTO       (default) per-thread register accumulation up to 8
  *                         shared components; beyond that the tensor cores

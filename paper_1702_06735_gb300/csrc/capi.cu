@@ -12,6 +12,7 @@
 
 #include "../../include/tdmix.h"
 #include "device_tables.hpp"
+#include "generate.cuh"
 #include "kernels.hpp"
 #include "model.hpp"
 
@@ -703,6 +704,145 @@ int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, in
       ctx->prof_ms[c] = 0;
       ctx->prof_n[c] = 0;
     }
+  }
+  return TDMIX_OK;
+}
+
+int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t seed, uint32_t stream, int flat,
+                   double* p_out, double* t_out, double* info) {
+  if (!ctx || n < 1 || !p_out || (!flat && !params)) return fail(ctx, TDMIX_ERR_ARG, "bad argument");
+  if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  cudaGetLastError();  // a failure left by earlier, unrelated work must not be reported here
+  if (!is_device_ptr(p_out) || (t_out && !is_device_ptr(t_out)))
+    return fail(ctx, TDMIX_ERR_ARG, "p_out and t_out must be device memory");
+  const GenOps* g = find_gen_ops(ctx->model.signature());
+  if (!g) return fail(ctx, TDMIX_ERR_UNSUPPORTED, "no generator compiled for this model structure");
+  int rc;
+  if (!flat && (rc = check_params(ctx, params))) return rc;
+  const CompiledModel& m = ctx->model;
+  GenArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.km = ctx->km;
+  if (!flat) std::memcpy(a.hp, params, m.n_params() * sizeof(double));
+  a.dm = ctx->d_model;
+  a.mD = m.parent_mass;
+  double msum = 0, cum[4];
+  for (int i = 0; i < 4; ++i) {
+    a.m[i] = m.masses[i];
+    msum += m.masses[i];
+    cum[i] = msum;
+  }
+  a.tecm = a.mD - msum;
+  if (!(a.tecm > 0)) return fail(ctx, TDMIX_ERR_ARG, "decay below threshold");
+  // GENBOD's bound of the product of breakup momenta: each at the largest
+  // parent and smallest subsystem mass
+  auto q = [](double M, double x, double y) {
+    const double l = (M * M - (x + y) * (x + y)) * (M * M - (x - y) * (x - y));
+    return l > 0 ? std::sqrt(l) / (2 * M) : 0.0;
+  };
+  double wtmax = 1.0;
+  for (int j = 1; j < 4; ++j) wtmax *= q(a.tecm + cum[j], cum[j - 1], m.masses[j]);
+  a.inv_wtmax = 1.0 / wtmax;
+  const double y = flat ? 0.0 : params[m.n_params() - 1];
+  a.lambda = (1.0 - std::fabs(y)) / m.tau;
+  a.key0 = uint32_t(seed);
+  a.key1 = uint32_t(seed >> 32);
+  a.flat = flat ? 1 : 0;
+  a.p_out = p_out;
+  a.t_out = t_out;
+  a.ld = n;
+  a.out_end = n;
+  cudaStream_t st = ctx->stream;
+  const int grid = 1024;
+  const int64_t batch = int64_t(grid) * kGenPerBlock;
+  std::vector<void*> bufs;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* p : bufs) cudaFree(p);
+  };
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    bufs.push_back(*p);
+    return true;
+  };
+  int64_t* d_pos = nullptr;
+  if (!alloc(reinterpret_cast<void**>(&a.mask), batch / 32 * sizeof(uint32_t)) ||
+      !alloc(reinterpret_cast<void**>(&a.block_count), grid * sizeof(uint32_t)) ||
+      !alloc(reinterpret_cast<void**>(&a.wmax), sizeof(unsigned long long)) ||
+      !alloc(reinterpret_cast<void**>(&d_pos), grid * sizeof(int64_t))) {
+    cleanup();
+    return fail(ctx, TDMIX_ERR_NOMEM, "generator buffers");
+  }
+  a.block_pos = d_pos;
+  std::vector<uint32_t> counts(grid);
+  std::vector<int64_t> pos(grid);
+  unsigned long long wbits = 0;
+  auto pass1 = [&](double* wmax_out) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(a.wmax, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = g->pass1(grid, st, a);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts.data(), a.block_count, grid * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&wbits, a.wmax, sizeof wbits, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    double w;
+    std::memcpy(&w, &wbits, sizeof w);
+    *wmax_out = w;
+    return e;
+  };
+  // pilot (model events): the envelope is 1.5 x the largest weight of one
+  // batch (4.2M candidates) drawn from a separate stream; the weight
+  // R e^{lambda t} has a long tail (narrow resonances), so a tighter
+  // headroom makes later batches exceed it and the sample be redrawn
+  double env = 0, wmax = 0;
+  cudaError_t e = cudaSuccess;
+  if (!flat) {
+    a.stream = stream ^ 0x80000000u;
+    a.env = 0.0;
+    a.cand0 = 0;
+    if ((e = pass1(&wmax)) != cudaSuccess) {
+      cleanup();
+      return fail(ctx, TDMIX_ERR_CUDA, std::string("generator pilot: ") + cudaGetErrorString(e));
+    }
+    if (!(wmax > 0) || !std::isfinite(wmax)) {
+      cleanup();
+      return fail(ctx, TDMIX_ERR_NONFINITE, "generator pilot: no positive finite weight");
+    }
+    env = 1.5 * wmax;
+  }
+  a.stream = stream;
+  int64_t have = 0, proposed = 0;
+  int restarts = 0;
+  while (have < n) {
+    a.env = env;
+    a.cand0 = proposed;
+    if ((e = pass1(&wmax)) != cudaSuccess) break;
+    if (!flat && wmax > env) {  // the envelope was exceeded: raise it and start again
+      if (++restarts > 4) {
+        cleanup();
+        return fail(ctx, TDMIX_ERR_NONFINITE, "generator envelope kept being exceeded");
+      }
+      env = 1.5 * wmax;
+      have = proposed = 0;
+      continue;
+    }
+    int64_t run = have;
+    for (int b = 0; b < grid; ++b) {
+      pos[b] = run;
+      run += counts[b];
+    }
+    if ((e = cudaMemcpyAsync(d_pos, pos.data(), grid * sizeof(int64_t), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      break;
+    if ((e = g->pass2(grid, st, a)) != cudaSuccess) break;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;  // pos[] is reused by the next batch
+    have = run;
+    proposed += batch;
+  }
+  cleanup();
+  if (e != cudaSuccess) return fail(ctx, TDMIX_ERR_CUDA, std::string("generator: ") + cudaGetErrorString(e));
+  if (info) {
+    info[0] = env;
+    info[1] = double(proposed);
+    info[2] = double(n) / double(proposed);
+    info[3] = restarts;
   }
   return TDMIX_OK;
 }

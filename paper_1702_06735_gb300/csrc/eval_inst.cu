@@ -4,6 +4,7 @@
 #include <string>
 
 #include "fused.cuh"
+#include "generate.cuh"
 #include "serve.cuh"
 #include "kernels.hpp"
 #include "shapes_gen.h"
@@ -116,6 +117,35 @@ struct Ops {
 };
 
 }  // namespace
+
+#if !TDMIX_PREC_F32
+namespace {
+template <class S>
+struct Gen {
+  static cudaError_t pass1(int grid, cudaStream_t st, const GenArgs& a) {
+    k_gen_pass1<S><<<grid, kGenThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t pass2(int grid, cudaStream_t st, const GenArgs& a) {
+    k_gen_pass2<S><<<grid, kGenThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+};
+}  // namespace
+
+// The generator evaluates the rate in double precision whatever the
+// precision of the context, so it is compiled once (here).
+const GenOps* find_gen_ops(const std::string& sig) {
+#define TDMIX_GEN_ENTRY(S)                                                    \
+  if (sig == shapes::S::sig()) {                                              \
+    static const GenOps o = {&Gen<shapes::S>::pass1, &Gen<shapes::S>::pass2}; \
+    return &o;                                                                \
+  }
+  TDMIX_FOR_EACH_SHAPE(TDMIX_GEN_ENTRY)
+#undef TDMIX_GEN_ENTRY
+  return nullptr;
+}
+#endif
 
 const ShapeOps* TDMIX_FIND(const std::string& sig) {
 #define TDMIX_SHAPE_ENTRY(S)                                                                  \

@@ -42,6 +42,16 @@ struct ShapeOps {
 // Table of the kernels' logarithm ({1/F, ln F} pairs, F = 1 + j/128).
 std::vector<double> make_log_table();
 
+struct GenArgs;
+// Launchers of the event generator of one model structure (generate.cuh):
+// pass 1 (accept bits, block counts, largest weight) and pass 2 (write the
+// accepted events), grid blocks of kGenPerBlock candidates each.
+struct GenOps {
+  cudaError_t (*pass1)(int grid, cudaStream_t st, const GenArgs& a);
+  cudaError_t (*pass2)(int grid, cudaStream_t st, const GenArgs& a);
+};
+const GenOps* find_gen_ops(const std::string& signature);
+
 // Specialisation compiled for a model signature, or null.
 const ShapeOps* find_shape_ops(const std::string& signature, bool f32);
 

@@ -9,6 +9,7 @@
 #include "../../include/tdmix.h"
 #include "eval.cuh"
 #include "kernels.hpp"
+#include "philox.cuh"
 
 namespace {
 
@@ -48,7 +49,25 @@ __global__ void k_test_math(int which, int64_t n, const double* __restrict__ in,
   }
 }
 
+__global__ void k_test_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                              uint32_t* out) {
+  const Philox4 r = philox4x32_10(Philox4{{c0, c1, c2, c3}}, k0, k1);
+  for (int i = 0; i < 4; ++i) out[i] = r.v[i];
+}
+
 }  // namespace
+
+extern "C" int tdmix_test_philox(const uint32_t* counter, const uint32_t* key, uint32_t* out) {
+  if (!counter || !key || !out) return TDMIX_ERR_ARG;
+  cudaGetLastError();
+  uint32_t* d = nullptr;
+  if (cudaMalloc(&d, 4 * sizeof(uint32_t)) != cudaSuccess) return TDMIX_ERR_NOMEM;
+  k_test_philox<<<1, 1>>>(counter[0], counter[1], counter[2], counter[3], key[0], key[1], d);
+  const bool ok = cudaGetLastError() == cudaSuccess &&
+                  cudaMemcpy(out, d, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(d);
+  return ok ? TDMIX_OK : TDMIX_ERR_CUDA;
+}
 
 extern "C" int tdmix_test_math(int which, int64_t n, const double* in, double* out) {
   if (n < 1 || !in || !out || which < 0 || which >= TDMIX_MATH_CODES) return TDMIX_ERR_ARG;

@@ -36,6 +36,8 @@ _SIGNATURES = {
     "tdmix_test_withhold_copy": (_c_i, [_c_p, _c_i]),
     "tdmix_recomputed_events": (_c_i, [_c_p, ctypes.POINTER(ctypes.c_int64)]),
     "tdmix_set_gram": (_c_i, [_c_p, _c_i]),
+    "tdmix_generate": (_c_i, [_c_p, _c_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, _c_i, _c_p, _c_p, _c_p]),
+    "tdmix_test_philox": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_test_math": (_c_i, [_c_i, ctypes.c_int64, _c_p, _c_p]),
     "tdmix_load_events": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_nll": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
@@ -88,6 +90,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 
 MATH_CODES = {"log_table": 0, "log_cuda": 1, "rcp_f64": 2, "div_f64": 3, "rcp_f32": 4, "div_f32": 5,
               "df_rcp": 6, "mix_tier0": 7, "mix_tier1": 8, "mix_tier2": 9}
+
+
+def test_philox(counter, key):
+    """Philox4x32-10 of the device generator (tdmix_test_philox)."""
+    lib = load_library()
+    c = np.asarray(counter, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    rc = lib.tdmix_test_philox(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise TDMixError(rc, "tdmix_test_philox")
+    return tuple(int(x) for x in out)
 
 
 def test_math(which: str, v) -> np.ndarray:
@@ -258,6 +272,24 @@ class TDMix:
         out = np.empty(2 * U * U)
         self._check(self._lib.tdmix_norm_matrix(self._ctx, out.ctypes.data))
         return (out[0::2] + 1j * out[1::2]).reshape(U, U)
+
+    def generate(self, n: int, seed: int, stream: int = 0, params=None, flat: bool = False, with_times: bool = True):
+        """n pseudo-events of the model at `params` (or flat phase space) on
+        the GPU: (momenta (n, 4, 4) and times (n,) as CUDA float64 tensors,
+        info dict)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        planes = torch.empty(16, n, dtype=torch.float64, device=dev)
+        t = torch.empty(n, dtype=torch.float64, device=dev) if with_times else None
+        p = None if flat else np.ascontiguousarray(np.asarray(params if params is not None else self.default_params(),
+                                                             dtype=np.float64))
+        info = np.zeros(4)
+        self._check(self._lib.tdmix_generate(self._ctx, None if p is None else p.ctypes.data, n, seed, stream,
+                                             int(flat), planes.data_ptr(), t.data_ptr() if t is not None else None,
+                                             info.ctypes.data))
+        p4 = planes.view(4, 4, n).permute(2, 0, 1)
+        return p4, t, {"envelope": float(info[0]), "candidates": int(info[1]), "efficiency": float(info[2]),
+                       "restarts": int(info[3])}
 
     GRAM_MODES = {"auto": 0, "registers": 1, "tensor": 2}
 

@@ -109,3 +109,48 @@ def grad_scale(model, data, t, mc, params, mc_weights=None):
     w = torch.ones(len(mm), dtype=torch.float64) if mc_weights is None else torch.as_tensor(mc_weights)
     S = Jd.abs().sum(0) + len(d) * (w[:, None] * Jm.abs()).sum(0) / (w * f).sum()
     return S.numpy()
+
+
+def projections(p4):
+    """The five variables of the four-body phase space used to display the
+    fit in Sec. 3.2: m12 = m(K+ pi-), m34 = m(pi+ pi-) (particles 0 1 and
+    2 3), the helicity cosines of particle 0 in the (0 1) rest frame and of
+    particle 2 in the (2 3) rest frame (each against its pair's direction in
+    the parent frame), and the angle phi between the two decay planes.
+    p4: (n, 4, 4) parent-frame momenta.  Returns (n, 5)."""
+    p4 = np.asarray(p4, dtype=np.float64)
+
+    def mass(P):
+        return np.sqrt(np.maximum(P[:, 0] ** 2 - (P[:, 1:] ** 2).sum(1), 0.0))
+
+    def helicity_cos(pa, P):
+        beta = P[:, 1:] / P[:, :1]
+        b2 = (beta ** 2).sum(1)
+        g = 1.0 / np.sqrt(1.0 - b2)
+        bp = (beta * pa[:, 1:]).sum(1)
+        k = np.where(b2 > 0, (g - 1.0) / np.where(b2 > 0, b2, 1.0) * bp, 0.0) - g * pa[:, 0]
+        v = pa[:, 1:] + k[:, None] * beta        # momentum in the pair's rest frame
+        d = P[:, 1:]
+        return (v * d).sum(1) / np.sqrt((v ** 2).sum(1) * (d ** 2).sum(1))
+
+    P12, P34 = p4[:, 0] + p4[:, 1], p4[:, 2] + p4[:, 3]
+    n1 = np.cross(p4[:, 0, 1:], p4[:, 1, 1:])
+    n2 = np.cross(p4[:, 2, 1:], p4[:, 3, 1:])
+    z = P12[:, 1:] / np.linalg.norm(P12[:, 1:], axis=1, keepdims=True)
+    phi = np.arctan2((np.cross(n1, n2) * z).sum(1), (n1 * n2).sum(1))
+    return np.stack([mass(P12), mass(P34), helicity_cos(p4[:, 0], P12), helicity_cos(p4[:, 2], P34), phi], axis=1)
+
+
+def binned_chi2(obs, ref, ref_w, bins, rng):
+    """Chi-square of an unweighted sample `obs` against the distribution of a
+    weighted reference sample, both histogrammed in `bins` over `rng`;
+    the reference's own statistical uncertainty is included.  Returns
+    (chi2, degrees of freedom)."""
+    ho, _ = np.histogram(obs, bins=bins, range=rng)
+    hw, _ = np.histogram(ref, bins=bins, range=rng, weights=ref_w)
+    hw2, _ = np.histogram(ref, bins=bins, range=rng, weights=ref_w ** 2)
+    scale = ho.sum() / hw.sum()
+    exp = hw * scale
+    var = exp + hw2 * scale ** 2
+    keep = exp > 5
+    return float((((ho - exp) ** 2)[keep] / var[keep]).sum()), int(keep.sum()) - 1
