@@ -265,18 +265,24 @@ int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, in
  * floating x, y) submit (sample, parameters) requests concurrently.  The
  * server keeps the model's resonance masses and widths fixed, so the MC
  * normalisation sums are computed once and every resident sample keeps its
- * per-event component cache.  A scheduler thread evaluates whatever is
- * pending as one batched kernel launch; requests that arrive meanwhile join
- * the next batch.  Samples are admitted into device memory by footprint
- * (2U component values + one decay time per event); when the budget binds,
- * least recently used samples without pending requests are evicted, and a
- * request whose sample cannot be admitted yet waits for memory to free up.
- * A request's result does not depend on which other requests share its
- * batch.  All functions are thread-safe. */
+ * per-event component cache.  Requests go to a device-resident loop: a
+ * persistent kernel on all but 16 SMs takes (request, chunk of event
+ * tiles) work items from a ring in page-locked, device-mapped memory as the
+ * host publishes them, so requests that arrive while others run are served
+ * at once, alongside them; the block finishing a request's last chunk
+ * writes its result and a completion flag back to mapped memory.  Samples
+ * are admitted into device memory by footprint (2U component values + one
+ * decay time per event) on a separate stream and thread, concurrently with
+ * the loop; when the budget binds, least recently used samples without
+ * pending requests are evicted, and a request whose sample cannot be
+ * admitted yet waits for memory to free up.  A request's result does not
+ * depend on which other requests are in flight (bitwise).  The loop stops
+ * itself after 20 ms without work and is relaunched by the next request;
+ * every device-side wait is bounded.  All functions are thread-safe. */
 typedef struct tdmix_server tdmix_server;
 
 /* hbm_budget_bytes: device memory allowed for resident samples;
- * max_slots: requests per batch at most (1 .. 1024). */
+ * max_slots: requests in flight at most (1 .. 1024). */
 int tdmix_server_create(const char* model_json, int precision, size_t hbm_budget_bytes, int max_slots,
                         tdmix_server** out);
 /* The shared phase-space MC sample (host or device memory, see
@@ -285,6 +291,12 @@ int tdmix_server_add_mc(tdmix_server* s, const tdmix_events* mc);
 /* Registers a data sample (copied to page-locked host memory; admitted to the
  * device on demand, and again after an eviction); *sample_id receives its id. */
 int tdmix_server_add_sample(tdmix_server* s, const tdmix_events* data, int* sample_id);
+/* Registers a sample that the server generates on the device each time it
+ * admits it (tdmix_generate with the model at `params`, n events, seed and
+ * stream): pseudo-experiments need no host copy and are regenerated
+ * identically after an eviction; *sample_id receives its id. */
+int tdmix_server_add_generated_sample(tdmix_server* s, const double* params, int64_t n, uint64_t seed,
+                                      uint32_t stream, int* sample_id);
 /* Queues an NLL + gradient evaluation of sample_id at params (host,
  * num_params doubles; masses and widths must equal the model's values,
  * else TDMIX_ERR_ARG).  *ticket identifies the request. */
@@ -301,6 +313,14 @@ int tdmix_server_stats(tdmix_server* s, double* p50_us, double* p99_us, double* 
 int tdmix_server_reset_stats(tdmix_server* s);
 /* Device memory currently held by resident samples. */
 int tdmix_server_resident_bytes(tdmix_server* s, size_t* bytes);
+/* State of the device-resident loop: info[0] launches so far, info[1]
+ * launches that ended on their own (a bounded wait gave up; their
+ * unfinished requests ran again), info[2] requests published, info[3] 1 if
+ * the loop is running, info[4] the device status bits of the last such
+ * launch (1: a tile copy did not arrive in time, 2: no work arrived within
+ * the loop's idle bound), info[5] how long it had run (microseconds);
+ * info holds 6 entries. */
+int tdmix_server_loop_info(tdmix_server* s, int64_t* info);
 const char* tdmix_server_last_error(const tdmix_server* s);
 /* Stops the scheduler (pending requests are dropped) and frees everything. */
 void tdmix_server_destroy(tdmix_server* s);

@@ -51,6 +51,7 @@ struct tdmix_ctx {
   double* d_sumt = nullptr;
   unsigned long long* d_trace = nullptr;  // per-block phase stamps of the last evaluation (tracing on)
   int64_t* d_ranges = nullptr;            // per-block MC tile ranges [num_sms + 1]
+  int64_t* d_zero_ranges = nullptr;       // [num_sms + 1] zeros: no MC tiles (data-only passes)
   double* d_logtab = nullptr;             // logarithm table of the kernels ({1/F, ln F} pairs)
   int64_t ranges_key[3] = {-1, -1, -1};   // (data tiles, MC tiles, grid) the ranges were made for
   double* last_result = nullptr;   // result vector the last evaluation wrote (d_result or d_result_map)
@@ -99,14 +100,18 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-void free_sample(Sample& s) {
-  for (void* p : s.owned) cudaFree(p);
+// Event buffers come from the stream-ordered allocator (cudaMallocAsync /
+// cudaFreeAsync on the context's stream): unlike cudaMalloc / cudaFree they
+// never wait for the whole device, so samples can be loaded and released
+// while a persistent kernel (the serving loop) runs.
+void free_sample(Sample& s, cudaStream_t st) {
+  for (void* p : s.owned) cudaFreeAsync(p, st);
   s.owned.clear();
   s = Sample{};
 }
 
 int dalloc(tdmix_ctx* ctx, Sample& s, void** p, size_t bytes) {
-  TDMIX_CK(cudaMalloc(p, bytes < 16 ? 16 : bytes));
+  TDMIX_CK(cudaMallocAsync(p, bytes < 16 ? 16 : bytes, ctx->stream));
   s.owned.push_back(*p);
   return TDMIX_OK;
 }
@@ -240,7 +245,7 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
     for (int c = 0; c < 4; ++c)
       if (!ev->p[a][c]) return fail(ctx, TDMIX_ERR_ARG, "missing momentum plane");
   if (is_data && !ev->t) return fail(ctx, TDMIX_ERR_ARG, "the data sample needs decay times");
-  free_sample(s);
+  free_sample(s, ctx->stream);
   const ShapeOps* ops = ctx->ops;
   const int64_t n = ev->n;
   const int64_t n_tiles = (n + kTileEvents - 1) / kTileEvents;
@@ -249,12 +254,12 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
   Momenta mom;
   std::vector<void*> temps;
   auto cleanup = [&]() {
+    for (void* p : temps) cudaFreeAsync(p, st);
     cudaStreamSynchronize(st);
-    for (void* p : temps) cudaFree(p);
   };
   auto fail_clean = [&](int code, const std::string& msg) {
     cleanup();
-    free_sample(s);
+    free_sample(s, st);
     return fail(ctx, code, msg);
   };
   // f64 device copy of a per-event host array (or the caller's device array)
@@ -264,7 +269,7 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
       return TDMIX_OK;
     }
     void* buf = nullptr;
-    if (cudaMalloc(&buf, size_t(n) * sizeof(double)) != cudaSuccess) return TDMIX_ERR_NOMEM;
+    if (cudaMallocAsync(&buf, size_t(n) * sizeof(double), st) != cudaSuccess) return TDMIX_ERR_NOMEM;
     temps.push_back(buf);
     if (cudaMemcpyAsync(buf, src, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
       return TDMIX_ERR_CUDA;
@@ -276,7 +281,7 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
       for (int c = 0; c < 4; ++c) mom.p[a][c] = ev->p[a][c];
   } else {
     void* buf = nullptr;
-    cudaError_t e = cudaMalloc(&buf, size_t(16) * n * sizeof(double));
+    cudaError_t e = cudaMallocAsync(&buf, size_t(16) * n * sizeof(double), st);
     if (e != cudaSuccess) return fail(ctx, TDMIX_ERR_NOMEM, "momentum staging buffer");
     temps.push_back(buf);
     for (int a = 0; a < 4; ++a)
@@ -324,7 +329,7 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
   if (!prc) prc = prof_mark(ctx, TDMIX_PROF_PRECOMPUTE, 1);
   if (prc) {
     cleanup();
-    free_sample(s);
+    free_sample(s, st);
     return prc;
   }
   double sum = 0;
@@ -335,14 +340,14 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
   cleanup();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    free_sample(s);
+    free_sample(s, st);
     return fail(ctx, TDMIX_ERR_CUDA, std::string("precompute: ") + cudaGetErrorString(e));
   }
   if (is_data) {
     ctx->sum_t = sum;
   } else if (w_dev) {
     if (!(sum > 0)) {
-      free_sample(s);
+      free_sample(s, st);
       return fail(ctx, TDMIX_ERR_ARG, "MC weights must have a positive sum");
     }
     ctx->inv_sum_w = 1.0 / sum;
@@ -357,8 +362,11 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
 // `result` receives [nll, N, n_bad or status, sum ln B, grad...] (device
 // or mapped host memory); out_nll / out_grad are optional second
 // destinations (device memory).
+// data_only: a full evaluation of the data tiles alone (components written to
+// the cache); the MC tiles are skipped, so its NLL and stored normalisation
+// are not meaningful (used to build component caches).
 int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool want_grad, double* rates,
-                 double* result, double* out_nll = nullptr, double* out_grad = nullptr) {
+                 double* result, double* out_nll = nullptr, double* out_grad = nullptr, bool data_only = false) {
   const CompiledModel& m = ctx->model;
   const int np = m.n_params(), nc = int(m.chains.size());
   cudaStream_t st = ctx->stream;
@@ -367,13 +375,13 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   for (int k = 2 * nc; k < 2 * nc + 2 * m.NR(); ++k) res_floating |= ctx->floating[k] != 0;
   // per-event rates always come from a full evaluation (the recomputation
   // of ill-conditioned events of the fp32 path runs there)
-  bool full = rates != nullptr || !host_params || !ctx->cache_valid || (want_grad && res_floating);
+  bool full = data_only || rates != nullptr || !host_params || !ctx->cache_valid || (want_grad && res_floating);
   if (host_params && !full) {
     for (int k = 0; k < 2 * m.NR(); ++k)
       if (params[2 * nc + k] != ctx->last_res[k]) full = true;
   }
   int rc;
-  const int64_t items = ctx->data.dev.n_tiles + (full ? ctx->mc.dev.n_tiles : 0);
+  const int64_t items = ctx->data.dev.n_tiles + (full && !data_only ? ctx->mc.dev.n_tiles : 0);
   const int grid = int(items < ctx->num_sms ? items : ctx->num_sms);
   // parameters travel in the kernel arguments (host callers) or are read
   // from the caller's device array
@@ -398,7 +406,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.sum_t = ctx->sum_t;
   a.inv_sum_w = ctx->inv_sum_w;
   a.trace = ctx->d_trace;
-  if (full) {
+  if (full && !data_only) {
     // Static, cost-balanced assignment of MC tiles to blocks: block q takes
     // data tiles q, q + grid, ... and MC tiles [range[q], range[q + 1]).
     const int64_t n_dt = ctx->data.dev.n_tiles, n_mt = ctx->mc.dev.n_tiles;
@@ -421,13 +429,15 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
       ctx->ranges_key[2] = grid;
     }
   }
-  a.mc_ranges = ctx->d_ranges;
+  a.mc_ranges = data_only ? ctx->d_zero_ranges : ctx->d_ranges;
 
   if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
   ctx->last_result = result;
   TDMIX_CK(ctx->ops->eval(full, want_grad, grid, st, a));
   if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 1))) return rc;
-  if (full) {
+  if (data_only) {
+    ctx->gram_valid = ctx->cache_valid = false;
+  } else if (full) {
     ctx->gram_valid = true;
     ctx->cache_valid = true;
     if (host_params) ctx->last_res.assign(params + 2 * nc, params + 2 * nc + 2 * m.NR());
@@ -475,7 +485,7 @@ int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* p
   int rc = load_sample(ctx, ev, true, ctx->data);
   if (rc) return rc;
   ctx->cache_valid = false;
-  if ((rc = enqueue_eval(ctx, params, true, false, nullptr, ctx->d_result))) return rc;
+  if ((rc = enqueue_eval(ctx, params, true, false, nullptr, ctx->d_result, nullptr, nullptr, true))) return rc;
   TDMIX_CK(cudaStreamSynchronize(ctx->stream));
   Sample& d = ctx->data;
   *cache = d.dev.cache;
@@ -483,7 +493,7 @@ int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* p
   *sum_t = ctx->sum_t;
   // keep the cache alive, free the planes and scratch
   for (void* p : d.owned)
-    if (p != d.dev.cache) cudaFree(p);
+    if (p != d.dev.cache) cudaFreeAsync(p, ctx->stream);
   d.owned.clear();
   d = Sample{};
   ctx->cache_valid = false;
@@ -498,7 +508,7 @@ int compute_mc_totals(tdmix_ctx* ctx, const double* params, const tdmix_events* 
   ctx->cache_valid = false;
   if ((rc = enqueue_eval(ctx, params, true, false, nullptr, ctx->d_result))) return rc;
   TDMIX_CK(cudaStreamSynchronize(ctx->stream));
-  free_sample(ctx->data);
+  free_sample(ctx->data, ctx->stream);
   ctx->cache_valid = false;
   return TDMIX_OK;
 }
@@ -546,6 +556,8 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   TDMIX_CK(cudaMalloc(&ctx->d_part, size_t(ctx->num_sms) * (ctx->ops->mc_width + ctx->ops->data_width) * 8 + 16));
   TDMIX_CK(cudaMalloc(&ctx->d_counter, sizeof(unsigned)));
   TDMIX_CK(cudaMalloc(&ctx->d_ranges, (ctx->num_sms + 1) * sizeof(int64_t)));
+  TDMIX_CK(cudaMalloc(&ctx->d_zero_ranges, (ctx->num_sms + 1) * sizeof(int64_t)));
+  TDMIX_CK(cudaMemset(ctx->d_zero_ranges, 0, (ctx->num_sms + 1) * sizeof(int64_t)));
   {
     const std::vector<double> lt = make_log_table();
     TDMIX_CK(cudaMalloc(&ctx->d_logtab, lt.size() * sizeof(double)));
@@ -757,11 +769,11 @@ int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t see
   const int64_t batch = int64_t(grid) * kGenPerBlock;
   std::vector<void*> bufs;
   auto cleanup = [&]() {
+    for (void* p : bufs) cudaFreeAsync(p, st);
     cudaStreamSynchronize(st);
-    for (void* p : bufs) cudaFree(p);
   };
   auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+    if (cudaMallocAsync(p, bytes, st) != cudaSuccess) return false;
     bufs.push_back(*p);
     return true;
   };
@@ -910,8 +922,9 @@ const char* tdmix_last_error(const tdmix_ctx* ctx) {
 void tdmix_destroy(tdmix_ctx* ctx) {
   if (!ctx) return;
   if (ctx->ops) cudaStreamSynchronize(ctx->stream);
-  free_sample(ctx->data);
-  free_sample(ctx->mc);
+  free_sample(ctx->data, ctx->stream);
+  free_sample(ctx->mc, ctx->stream);
+  if (ctx->ops) cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->d_model);
   cudaFree(ctx->d_result);
   cudaFree(ctx->d_gram);
@@ -920,6 +933,7 @@ void tdmix_destroy(tdmix_ctx* ctx) {
   cudaFree(ctx->d_part);
   cudaFree(ctx->d_trace);
   cudaFree(ctx->d_ranges);
+  cudaFree(ctx->d_zero_ranges);
   cudaFree(ctx->d_logtab);
   if (ctx->h_result) cudaFreeHost(ctx->h_result);
   for (int c = 0; c < TDMIX_PROF_CLASSES; ++c)

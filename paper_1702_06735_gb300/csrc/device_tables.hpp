@@ -99,38 +99,59 @@ constexpr int kTracePhases = 8;
 constexpr int kDataTileCostF32 = 4;
 constexpr int kDataTileCostF64 = 1;
 
-constexpr int kServeMaxChunks = 256;     // chunks per request at most
-constexpr int kServeMaxRequests = 1024;  // requests per batch at most
-
-// One request of a serving batch (see serve.cuh).
-struct ServeReq {
-  const void* cache;     // tile-major component cache with decay times (SampleDev::cache)
-  int64_t n;
-  int64_t tile_bytes;    // bytes of one cache tile
-  int32_t chunk_begin;   // first row of this request in the partial array
-  int32_t n_chunks;
-  int32_t chunk_tiles;   // tiles per chunk (the last chunk may have fewer)
-  int32_t n_tiles;
-  double sum_t;
-};
-
-struct ServeArgs {
-  const ServeReq* reqs;
-  int n_req;
-  int total_chunks;
-  const double* params;     // [n_req][n_params]
-  ModelConst km;
-  const double* mc_cols;    // MC column totals of the fixed model
-  double inv_sum_w;
-  void* part;               // float2 [total_chunks][WD] chunk partials
-  unsigned* counters;       // [n_req] chunks finished (returned to 0)
-  double* results;          // [n_req][kResHeader + n_params]
-  int* err;
-  const void* logtab;       // logarithm table (as in EvalArgs)
-};
-
 // Result vector written by the evaluation kernel:
 // [nll, N, n_bad or status, sum ln B, data events recomputed in double-float, grad...]
 constexpr int kResHeader = 5;
+
+constexpr int kServeMaxChunks = 256;     // chunks per request at most
+constexpr int kServeMaxSlots = 1024;     // requests in flight at most
+constexpr int kServeRingCap = 1 << 16;   // ring entries per launch of the serving loop
+
+// One request slot of the serving loop (mapped, page-locked host memory;
+// written by the host before the request is published, read by the device;
+// the device writes the result and then `done`).  A slot is reused only
+// after its request finished.
+struct ServeSlot {
+  const void* cache;     // tile-major component cache with decay times (SampleDev::cache)
+  int64_t n;
+  int64_t tile_bytes;    // bytes of one cache tile
+  int32_t n_chunks;
+  int32_t chunk_tiles;   // tiles per chunk (the last chunk may have fewer)
+  int32_t n_tiles;
+  int32_t pad;
+  double sum_t;
+  double params[kMaxParams];
+  double result[kResHeader + kMaxParams];  // [nll, N, n_bad or status, sum ln B, n recomputed, grad...]
+  unsigned long long done;            // ring entry + 1 of the last request finished in this slot
+};
+
+// Ring of the serving loop (mapped host memory): entry e of a launch is
+// slot[e - head]; the host publishes entries by a release store of `tail`
+// and stops the loop with `stop`.
+struct ServeRing {
+  unsigned long long tail;
+  unsigned stop;
+  unsigned pad;
+  int32_t slot[kServeRingCap];
+};
+
+// Arguments of the persistent serving loop (grid constant).
+struct ServeLoopArgs {
+  ServeRing* ring;            // mapped
+  ServeSlot* slots;           // mapped, [kServeMaxSlots]
+  unsigned* claimed;          // device, [kServeRingCap]: chunks claimed per entry (zero at launch)
+  unsigned* finished;         // device, [kServeRingCap]: chunks finished per entry (zero at launch)
+  unsigned long long* low;    // device: the oldest entry with unclaimed chunks (head at launch)
+  unsigned long long head;    // first entry of this launch
+  ModelConst km;
+  const double* mc_cols;      // MC column totals of the fixed model
+  double inv_sum_w;
+  void* part;                 // float2 [kServeMaxSlots][kServeMaxChunks][row stride] chunk partials
+  int* status;                // device: 1 if a bounded wait gave up, 2 if the loop idled out
+  const void* logtab;         // logarithm table (as in EvalArgs)
+  unsigned long long idle_ns; // bound of one wait for new work
+};
+
+
 
 }  // namespace tdmix

@@ -102,14 +102,13 @@ struct Ops {
     }
     return cudaErrorNotSupported;
   }
-  static cudaError_t serve(bool grad, int grid, cudaStream_t st, const ServeArgs& a) {
+  static cudaError_t serve(int grid, cudaStream_t st, const ServeLoopArgs& a) {
     if constexpr (kOk) {
       const int smem = ServeLayout<Prec, S>::smem_bytes();
-      static SmemLimit seen_g, seen_n;
-      auto kern = grad ? k_serve<Prec, S, true> : k_serve<Prec, S, false>;
-      const cudaError_t e = allow_smem(kern, smem, grad ? seen_g : seen_n);
+      static SmemLimit seen;
+      const cudaError_t e = allow_smem(k_serve_loop<Prec, S, true>, smem, seen);
       if (e != cudaSuccess) return e;
-      kern<<<grid, kTile, smem, st>>>(a);
+      k_serve_loop<Prec, S, true><<<grid, kTile, smem, st>>>(a);
       return cudaGetLastError();
     }
     return cudaErrorNotSupported;
@@ -154,7 +153,8 @@ const ShapeOps* TDMIX_FIND(const std::string& sig) {
     static const ShapeOps o = {shapes::S::sig(), shapes::S::U, shapes::S::NR, LY_::WMC, LY_::WD, \
                                LY_::NPL_FULL, LY_::data_tile_bytes(), LY_::mc_tile_bytes(false), \
                                LY_::mc_tile_bytes(true), LY_::cache_tile_bytes(),               \
-                               &Ops<shapes::S>::eval, &Ops<shapes::S>::serve};                \
+                               &Ops<shapes::S>::eval, &Ops<shapes::S>::serve,                 \
+                               ServeLayout<Prec, shapes::S>::WR};                             \
     return &o;                                                                                \
   }
   TDMIX_FOR_EACH_SHAPE(TDMIX_SHAPE_ENTRY)

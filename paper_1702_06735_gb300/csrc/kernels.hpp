@@ -35,8 +35,9 @@ struct ShapeOps {
   int n_planes;    // event planes per tile (NPL)
   int64_t data_tile_bytes, mc_tile_bytes, mc_tile_bytes_weighted, cache_tile_bytes;
   cudaError_t (*eval)(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a);
-  // batched evaluation of serving requests (see serve.cuh)
-  cudaError_t (*serve)(bool grad, int grid, cudaStream_t st, const ServeArgs& a);
+  // the persistent serving loop (see serve.cuh)
+  cudaError_t (*serve)(int grid, cudaStream_t st, const ServeLoopArgs& a);
+  int serve_row_stride;  // float2 entries per chunk-partial row
 };
 
 // Table of the kernels' logarithm ({1/F, ln F} pairs, F = 1 + j/128).

@@ -1,20 +1,34 @@
-// Batched evaluation of many likelihood requests (serving).
+// Device-resident serving loop: many likelihood requests from concurrent
+// minimisers (the paper's sensitivity study fits pseudo-experiments with a
+// fixed model and floating x, y, Sec. 4).
 //
-// A request is (sample, parameter vector) with the amplitude model's masses
-// and widths fixed, so each resident sample keeps its per-event component
-// cache and the MC normalisation sums are shared by all requests.  One
-// persistent kernel evaluates a whole batch: the work items are chunks of
-// consecutive event tiles of one request; a block takes chunks b, b + grid,
-// ...  Each chunk's partial sums go to its own row, and the block that
-// finishes the last chunk of a request sums that request's rows in chunk
-// order and forms its NLL and gradient.  The chunk partition of a request
-// depends only on its size, so a request's result does not depend on which
-// other requests share the batch.
+// A request is (sample, parameter vector) with the model's masses and
+// widths fixed, so each resident sample keeps its per-event component cache
+// and the MC normalisation sums are shared by all requests.  The host
+// writes a request into a slot of page-locked, device-mapped memory and
+// publishes it as the next ring entry (a release store of the ring's tail).
+// A persistent kernel (one block per SM, leaving some SMs to admission and
+// generation work) takes work items (entry, chunk of consecutive event
+// tiles) as they appear:
+//   * thread 0 of a block claims a chunk of the entry at its cursor with an
+//     atomic counter and moves the cursor to the next entry (round robin
+//     over the entries with unclaimed chunks, so a short request published
+//     while a long one runs is served at once);
+//   * the block evaluates the chunk from the cached components (Eq. (mix),
+//     ln B, adjoint) and writes its partial row;
+//   * the block that finishes a request's last chunk sums the request's
+//     rows in chunk order, forms the NLL and gradient into the slot, makes
+//     them visible system-wide and then stores `done` with release
+//     semantics.
+// The chunk partition of a request depends only on its size and its rows
+// are summed in chunk order, so a result does not depend on which other
+// requests are in flight.  Every wait is bounded: a wait for new work gives
+// up after idle_ns (status 2) and the block exits; the host stops the loop
+// (ring.stop) when it has nothing in flight.
 #pragma once
 #include "fused.cuh"
 
 namespace tdmix {
-
 
 template <class P, class S>
 struct ServeLayout {
@@ -32,8 +46,24 @@ struct ServeLayout {
   }
 };
 
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_sys(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 template <class P, class S, bool GRAD>
-__global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ ServeArgs a) {
+__global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__ ServeLoopArgs a) {
   using T = typename P::T;
   using LY = ServeLayout<P, S>;
   constexpr int U = S::U, NR = S::NR, WD = LY::WD, WR = LY::WR, TE = kTile, ES = int(sizeof(T));
@@ -47,56 +77,107 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
   __shared__ int red_bad[kTile / 32];
   __shared__ float2 rowp[WD];
   __shared__ double colsum[WMC + WD];
-  __shared__ int chunk_start[kServeMaxRequests + 1];
-  __shared__ unsigned is_last;
-  __shared__ int s_timed_out;
   __shared__ double2 logtab[kLogTable];
+  __shared__ long long s_entry;
+  __shared__ int s_chunk, s_slot;
+  __shared__ unsigned s_last;
+  __shared__ ServeSlot s_req;  // the request's fields (one read of mapped memory)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int G = gridDim.x;
   unsigned char* stage[2] = {smem_raw, smem_raw + LY::stage_bytes};
-  for (int r = tid; r < a.n_req; r += blockDim.x) chunk_start[r] = a.reqs[r].chunk_begin;
   for (int j = tid; j < kLogTable; j += blockDim.x) logtab[j] = static_cast<const double2*>(a.logtab)[j];
   if (tid == 0) {
-    chunk_start[a.n_req] = a.total_chunks;
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
   const int np = a.km.n_params, nc = a.km.n_chains;
-  uint32_t uses = 0;  // completed barrier phases (both stages), for parity tracking
-  bool failed = false;
+  uint32_t uses = 0;                    // completed stage phases (both stages), for parity tracking
+  unsigned long long cursor = a.head;   // thread 0: next entry to try
+  float2* part_all = static_cast<float2*>(a.part);
 
-  for (int c = blockIdx.x; c < a.total_chunks && !failed; c += G) {
-    int lo = 0, hi = a.n_req;  // request r with chunk_start[r] <= c < chunk_start[r + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) / 2;
-      if (chunk_start[mid] <= c) lo = mid;
-      else hi = mid;
+  for (;;) {
+    // ---- thread 0 claims the next chunk: (entry, chunk), or stops
+    if (tid == 0) {
+      long long e = -1;
+      int c = 0, slot = 0;
+      unsigned long long idle_since = 0;
+      for (;;) {
+        if (ld_relaxed_sys(&a.ring->stop)) break;
+        const unsigned long long tail = ld_acquire_sys(&a.ring->tail);
+        const unsigned long long low = *static_cast<volatile unsigned long long*>(a.low);
+        if (cursor < low || cursor >= tail) cursor = low;  // round robin over [low, tail)
+        if (cursor >= tail) {                                // every published chunk is claimed
+          const unsigned long long now = global_ns();
+          if (idle_since == 0) {
+            idle_since = now;
+          } else if (now - idle_since > a.idle_ns) {
+            atomicOr(a.status, 2);
+            break;
+          }
+          __nanosleep(200);
+          continue;
+        }
+        idle_since = 0;
+        const int idx = int(cursor - a.head);
+        const int sl = a.ring->slot[idx];
+        const int nch = a.slots[sl].n_chunks;
+        const unsigned k = atomicAdd(&a.claimed[idx], 1u);
+        if (k < unsigned(nch)) {
+          e = (long long)cursor;
+          c = int(k);
+          slot = sl;
+          ++cursor;
+          break;
+        }
+        // this entry has no unclaimed chunk left; only the oldest such entry
+        // moves `low` on (a newer one being exhausted says nothing about
+        // the older entries the round robin still has to visit)
+        atomicCAS(a.low, cursor, cursor + 1);
+        ++cursor;
+      }
+      s_entry = e;
+      s_chunk = c;
+      s_slot = slot;
+      if (e >= 0) {
+        const ServeSlot& q = a.slots[slot];
+        s_req.cache = q.cache;
+        s_req.n = q.n;
+        s_req.tile_bytes = q.tile_bytes;
+        s_req.n_chunks = q.n_chunks;
+        s_req.chunk_tiles = q.chunk_tiles;
+        s_req.n_tiles = q.n_tiles;
+        s_req.sum_t = q.sum_t;
+      }
     }
-    const int r = lo;
-    const ServeReq q = a.reqs[r];
-    const int lc = c - q.chunk_begin;
-    const int t0 = lc * q.chunk_tiles;
-    const int t1 = min(t0 + q.chunk_tiles, q.n_tiles);
+    __syncthreads();
+    const long long e = s_entry;
+    if (e < 0) break;
+    const int c = s_chunk, slot = s_slot, eidx = int(e - (long long)a.head);
+    const int t0 = c * s_req.chunk_tiles;
+    const int t1 = min(t0 + s_req.chunk_tiles, s_req.n_tiles);
     const int ntl = t1 - t0;
+    const void* cache = s_req.cache;
+    const int64_t tile_bytes = s_req.tile_bytes, n_ev = s_req.n;
     auto issue = [&](int j, uint32_t use) {  // tile t0 + j into stage use & 1 (one bulk copy)
       const int st = int(use & 1);
-      mbar_arrive_expect_tx(&bars[st], uint32_t(q.tile_bytes));
-      bulk_g2s(stage[st], static_cast<const unsigned char*>(q.cache) + int64_t(t0 + j) * q.tile_bytes,
-               uint32_t(q.tile_bytes), &bars[st]);
+      mbar_arrive_expect_tx(&bars[st], uint32_t(tile_bytes));
+      bulk_g2s(stage[st], static_cast<const unsigned char*>(cache) + int64_t(t0 + j) * tile_bytes,
+               uint32_t(tile_bytes), &bars[st]);
     };
     if (tid == 0) {
       issue(0, uses);
       if (ntl > 1) issue(1, uses + 1);
     }
-    derive_load<T, U>(a.params + size_t(r) * np, nullptr, a.km, cc, bc);
+    derive_load<T, U>(a.slots[slot].params, nullptr, a.km, cc, bc);
     __syncthreads();
     derive_compute<T, U, NR>(a.km, cc, bc);
     __syncthreads();
 
     double lnb = 0.0;  // sum ln B = lnb + lexp ln 2
     int bad = 0, lexp = 0;
+    bool failed = false;
+    int failed_at = 0;
     T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
@@ -105,10 +186,11 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       const bool ok = mbar_wait_bounded(&bars[st], (uses >> 1) & 1u, kWaitNs);
       if (__syncthreads_or(!ok)) {
         failed = true;
+        failed_at = j;
         break;
       }
       const int64_t i = int64_t(t0 + j) * TE + tid;
-      if (i < q.n) {
+      if (i < n_ev) {
         const T* sbase = reinterpret_cast<const T*>(stage[st]);
         const double t_e = reinterpret_cast<const double*>(stage[st] + 2 * U * TE * ES)[tid];
         EventCore<P, S> ev;
@@ -137,11 +219,16 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       if (tid == 0 && j + 2 < ntl) issue(j + 2, uses + 2);
     }
     if (failed) {
+      // the copies of tiles failed_at and failed_at + 1 (if any) are in
+      // flight: let them land before shared memory is reused, and count
+      // their stage phases
+      const uint32_t in_flight = ntl - failed_at > 1 ? 2u : 1u;
       if (tid == 0) {
-        atomicOr(a.err, 1);
-        for (uint32_t u = uses; u < uses + 2; ++u) mbar_wait_bounded(&bars[u & 1], (u >> 1) & 1u, kWaitNs);
+        atomicOr(a.status, 1);
+        for (uint32_t u = uses; u < uses + in_flight; ++u) mbar_wait_bounded(&bars[u & 1], (u >> 1) & 1u, kWaitNs);
       }
       __syncthreads();
+      uses += in_flight;
     }
     // chunk partial -> its row (double-float; see block_sum_df)
     {
@@ -163,7 +250,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       }
       block_sum_df<T, 2 + 4 * U>(vt, red, rowp + 2);  // ends with a barrier
     }
-    float2* part = static_cast<float2*>(a.part);
+    float2* part = part_all + size_t(slot) * kServeMaxChunks * WR;
     if (tid == 0) {
       double sl = 0;
       int sb = 0;
@@ -179,46 +266,44 @@ __global__ void __launch_bounds__(kTile, 1) k_serve(const __grid_constant__ Serv
       part[size_t(c) * WR + v] = v < 4 + 4 * U ? rowp[v] : make_float2(0.f, 0.f);
     __threadfence();
     __syncthreads();
-    if (tid == 0) is_last = atomicAdd(a.counters + r, 1u) == unsigned(q.n_chunks - 1);
+    if (tid == 0) s_last = atomicAdd(&a.finished[eidx], 1u) == unsigned(s_req.n_chunks - 1);
     __syncthreads();
-    if (!is_last) continue;
-    // ---- last chunk of request r: sum its rows in chunk order, then the likelihood
+    if (!s_last) continue;
+    // ---- last chunk of the request: sum its rows in chunk order, then the likelihood
     __threadfence();
     float2* sp = reinterpret_cast<float2*>(smem_raw);
+    const int nch = s_req.n_chunks;
     if (tid == 0) {
       asm volatile("fence.proxy.async.global;" ::: "memory");
       mbar_init(&bars[2], 1);
       mbar_fence_init();
-      const uint32_t bytes = uint32_t(q.n_chunks) * uint32_t(WR) * 8u;  // a multiple of 16
+      const uint32_t bytes = uint32_t(nch) * uint32_t(WR) * 8u;  // a multiple of 16
       mbar_arrive_expect_tx(&bars[2], bytes);
-      bulk_g2s(sp, part + size_t(q.chunk_begin) * WR, bytes, &bars[2]);  // 16-byte aligned
+      bulk_g2s(sp, part, bytes, &bars[2]);  // 16-byte aligned
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(&bars[2], 0, kWaitNs);
-    if (__syncthreads_or(!ok) && tid == 0) atomicOr(a.err, 1);
+    if (__syncthreads_or(!ok) && tid == 0) atomicOr(a.status, 1);
     for (int v = tid; v < WMC; v += blockDim.x) colsum[v] = a.mc_cols[v];
     for (int v = tid; v < WD; v += blockDim.x) {
-      float s = 0.f, e = 0.f;
-      for (int row = 0; row < q.n_chunks; ++row) {
+      float s = 0.f, er = 0.f;
+      for (int row = 0; row < nch; ++row) {
         const float2 x = sp[size_t(row) * WR + v];
-        float t, er;
-        two_sum(s, x.x, t, er);
+        float t, err;
+        two_sum(s, x.x, t, err);
         s = t;
-        e += er + x.y;
+        er += err + x.y;
       }
-      colsum[WMC + v] = double(s) + double(e);
-    }
-    if (tid == 0) {
-      // a bounded wait that gave up anywhere in the batch is reported (once)
-      s_timed_out = *static_cast<volatile int*>(a.err);
-      if (s_timed_out) *a.err = 0;
-      a.counters[r] = 0u;
+      colsum[WMC + v] = double(s) + double(er);
     }
     __syncthreads();
-    finish_likelihood<S>(a.results + size_t(r) * (kResHeader + np), nullptr, nullptr, nc, np, cc, colsum,
-                         colsum + WMC, double(q.n), q.sum_t, a.inv_sum_w, GRAD, false, s_timed_out, logtab, nullptr);
+    const int timed_out = *static_cast<volatile int*>(a.status) & 1;
+    finish_likelihood<S>(a.slots[slot].result, nullptr, nullptr, nc, np, cc, colsum, colsum + WMC, double(n_ev),
+                         s_req.sum_t, a.inv_sum_w, GRAD, false, timed_out, logtab, nullptr);
+    __threadfence_system();
     __syncthreads();
-    // the bulk-copy target overlapped the stages: stages restart clean below
+    if (tid == 0) st_release_sys(&a.slots[slot].done, (unsigned long long)(e + 1));
+    // the row copy overlapped the stages; later chunks refill them from scratch
   }
 }
 

@@ -50,6 +50,9 @@ _SIGNATURES = {
     "tdmix_server_create": (_c_i, [ctypes.c_char_p, _c_i, ctypes.c_size_t, _c_i, ctypes.POINTER(_c_p)]),
     "tdmix_server_add_mc": (_c_i, [_c_p, _c_p]),
     "tdmix_server_add_sample": (_c_i, [_c_p, _c_p, ctypes.POINTER(_c_i)]),
+    "tdmix_server_add_generated_sample": (_c_i, [_c_p, _c_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                                 ctypes.POINTER(_c_i)]),
+    "tdmix_server_loop_info": (_c_i, [_c_p, _c_p]),
     "tdmix_server_submit": (_c_i, [_c_p, _c_i, _c_p, ctypes.POINTER(ctypes.c_uint64)]),
     "tdmix_server_wait": (_c_i, [_c_p, ctypes.c_uint64, _c_p, _c_p, ctypes.c_double]),
     "tdmix_server_stats": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
@@ -376,6 +379,21 @@ class TDMixServer:
         sid = ctypes.c_int()
         self._check(self._lib.tdmix_server_add_sample(self._s, ctypes.byref(ev), ctypes.byref(sid)))
         return sid.value
+
+    def add_generated_sample(self, params, n: int, seed: int, stream: int) -> int:
+        """A pseudo-experiment of n events generated on the device at each
+        admission from the model at `params` (seed, stream)."""
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        sid = ctypes.c_int()
+        self._check(self._lib.tdmix_server_add_generated_sample(self._s, p.ctypes.data, n, seed, stream,
+                                                                ctypes.byref(sid)))
+        return sid.value
+
+    def loop_info(self) -> dict:
+        v = np.zeros(6, dtype=np.int64)
+        self._check(self._lib.tdmix_server_loop_info(self._s, v.ctypes.data))
+        return {"launches": int(v[0]), "abnormal_exits": int(v[1]), "published": int(v[2]), "running": bool(v[3]),
+                "last_exit_status": int(v[4]), "last_exit_after_us": int(v[5])}
 
     def submit(self, sample_id: int, params) -> int:
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))

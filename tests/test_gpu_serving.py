@@ -1,6 +1,7 @@
 """Serving: batched, continuously admitted NLL + gradient requests from many
 concurrent clients (fixed model, floating coefficients and x, y)."""
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -171,3 +172,85 @@ def test_requests_that_move_the_model_or_leave_the_domain():
         s.wait(987654321, 0.01)
     assert e.value.code == -1
     s.close()
+
+
+def test_request_published_mid_run_finishes_before_an_earlier_long_one():
+    """Continuous batching on the device: a long request (4,000,000 events,
+    256 chunks, about two rounds of the loop's blocks) is running when a
+    short one (1,000 events) is published; blocks that finish a chunk take
+    the newest entry's chunks in turn, so the short request completes first.
+    Both samples are resident before the timing starts."""
+    from paper_1702_06735_gb300.tdmix import TDMixServer
+    m = tdamp.load_model(model_path("d0_k3pi_full"))
+    mc = samples.flat_phase_space(20_000, samples.rng(31, samples.STREAM_MC))
+    g = samples.rng(31, samples.STREAM_DATA)
+    big = samples.flat_phase_space(4_000_000, g)
+    big_t = samples.exponential_times(len(big), 1.0 / samples.TAU_D, g)
+    small, small_t = big[:1000], big_t[:1000]
+    s = TDMixServer("d0_k3pi_full", "fp64", hbm_budget_bytes=1 << 32, max_slots=16)
+    s.add_mc(mc)
+    id_big, id_small = s.add_sample(big, big_t), s.add_sample(small, small_t)
+    p = m.default_params().numpy()
+    s.evaluate(id_big, p, timeout_s=600)
+    s.evaluate(id_small, p, timeout_s=600)
+    order = []
+
+    def wait(tag, tk):
+        s.wait(tk, timeout_s=600)
+        order.append(tag)
+    t_big = s.submit(id_big, p)
+    time.sleep(2e-4)
+    t_small = s.submit(id_small, p)
+    th = [threading.Thread(target=wait, args=("big", t_big)), threading.Thread(target=wait, args=("small", t_small))]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    info = s.loop_info()
+    s.close()
+    print(f"\nloop: {info}")
+    assert order == ["small", "big"], order
+    assert info["abnormal_exits"] == 0, info
+
+
+def test_generated_samples_match_a_context_on_the_same_events():
+    """A pseudo-experiment generated on the device at admission gives the
+    same likelihood as a context loaded with the same generated events."""
+    from paper_1702_06735_gb300.tdmix import TDMix, TDMixServer
+    m = tdamp.load_model(model_path(NAME))
+    mc = samples.flat_phase_space(20_000, samples.rng(32, samples.STREAM_MC))
+    gen = m.default_params().numpy()
+    s = TDMixServer(NAME, "fp64", hbm_budget_bytes=1 << 30, max_slots=16)
+    s.add_mc(mc)
+    sid = s.add_generated_sample(gen, 30_000, seed=77, stream=5)
+    p = _params(m, np.random.default_rng(9))
+    v, gr = s.evaluate(sid, p)
+    c = TDMix(NAME, "fp64")
+    p4, t, _ = c.generate(30_000, seed=77, stream=5, params=gen)
+    c.load_events(p4, t, mc)
+    mask = m.floating_mask().numpy().astype(np.int32)
+    nc = len(m.chains)
+    mask[2 * nc:2 * nc + 2 * len(m.resonances)] = 0
+    c.set_floating(mask)
+    v0, g0 = c.nll(p)
+    c.close()
+    info = s.loop_info()
+    s.close()
+    assert abs(v - v0) <= 1e-12 * abs(v0)
+    assert np.abs(gr - g0).max() <= 1e-10 * np.abs(g0).max()
+    assert info["launches"] >= 1
+
+
+def test_loop_stops_when_idle_and_restarts():
+    m, toys, mc = _toys(2, 33)
+    s = _server("fp32", mc)
+    ids = [s.add_sample(p4, t) for p4, t in toys]
+    p = m.default_params().numpy()
+    a = s.evaluate(ids[0], p)
+    time.sleep(0.2)
+    assert not s.loop_info()["running"]
+    b = s.evaluate(ids[0], p)
+    info = s.loop_info()
+    s.close()
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    assert info["launches"] >= 2 and info["abnormal_exits"] == 0
