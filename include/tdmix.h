@@ -154,26 +154,36 @@ int tdmix_norm_matrix(tdmix_ctx* ctx, double* I_out);
 /* Pseudo-events of the context's model on the GPU (Sec. 3.1: flat
  * phase-space points and time-dependent pseudo-events by accept/reject).
  * Candidates are flat four-body phase-space points (GENBOD, F. James, CERN
- * 68-15) with decay times t ~ Exp((1 - |y|) Gamma); with flat == 0 each is
- * kept with probability R e^{(1-|y|) Gamma t} / env, R = e^{-Gamma t} B the
- * rate of Eq. (mix) at `params` (double precision, whatever the context's
- * precision), env 1.5 times the largest weight of a pilot batch (raised
- * and the sample redrawn, at most four times, if a later weight exceeds
- * it); with flat != 0 every phase-space point is kept and t is 0.  Random
- * numbers: Philox4x32-10 (Salmon et al., SC'11) with key `seed`, counter
- * (candidate index, stream, draw), so the sample depends only on (seed,
- * stream, params, n) and is written in candidate order.
- *   params  host, num_params doubles (ignored when flat)
+ * 68-15) with decay times t ~ Exp((1 - |y|) Gamma); without TDMIX_GEN_FLAT
+ * each is kept with probability R e^{(1-|y|) Gamma t} / env, R = e^{-Gamma t} B
+ * the rate of Eq. (mix) at `params` (double precision, whatever the
+ * context's precision), env 1.5 times the largest weight of a pilot batch
+ * (raised and the sample redrawn, at most four times, if a later weight
+ * exceeds it); with TDMIX_GEN_FLAT every phase-space point is kept and t
+ * is 0.  Candidates are first weighed in single precision with an error
+ * band (1e-3 of the weight plus 1e-4 of its cancellation-free scale), and
+ * only those whose decision falls inside the band are weighed in double
+ * precision: the decisions of the double-precision rate at a fraction of
+ * its cost; TDMIX_GEN_FP64_ONLY weighs every candidate in double precision
+ * (the same sample, slower).  Random numbers: Philox4x32-10 (Salmon et al.,
+ * SC'11) with key `seed`, counter (candidate index, stream, draw), so the
+ * sample depends only on (seed, stream, params, n) and is written in
+ * candidate order.
+ *   params  host, num_params doubles (ignored with TDMIX_GEN_FLAT)
+ *   flags   TDMIX_GEN_FLAT, TDMIX_GEN_FP64_ONLY (bitwise or)
  *   p_out   device, 16 planes of n doubles: component c (E, px, py, pz) of
  *           final-state particle a at p_out[(4a + c) n + i] (the layout of
  *           tdmix_events with on_device = 1)
  *   t_out   device, n decay times (ps), or NULL
  *   info    host, 4 doubles or NULL: envelope, candidates drawn, accepted
- *           fraction, envelope raises
+ *           fraction, envelope raises; a positive info[0] on entry is used
+ *           as the envelope instead of a pilot (pass the envelope of an
+ *           earlier call at the same parameters: samples then depend on it)
  * Synchronises with the context's stream; allocates temporary device
- * buffers.  TDMIX_ERR_NONFINITE if the pilot finds no positive finite rate
- * or the envelope keeps being exceeded. */
-int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t seed, uint32_t stream, int flat,
+ * buffers (stream-ordered).  TDMIX_ERR_NONFINITE if the pilot finds no
+ * positive finite rate or the envelope keeps being exceeded. */
+enum { TDMIX_GEN_FLAT = 1, TDMIX_GEN_FP64_ONLY = 2 };
+int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t seed, uint32_t stream, int flags,
                    double* p_out, double* t_out, double* info);
 
 /* Philox4x32-10 of the generator for one (counter, key) (self-test entry;
@@ -294,7 +304,9 @@ int tdmix_server_add_sample(tdmix_server* s, const tdmix_events* data, int* samp
 /* Registers a sample that the server generates on the device each time it
  * admits it (tdmix_generate with the model at `params`, n events, seed and
  * stream): pseudo-experiments need no host copy and are regenerated
- * identically after an eviction; *sample_id receives its id. */
+ * identically after an eviction; *sample_id receives its id.  The
+ * generator's envelope is found once per set of generating parameters and
+ * reused for the samples that share them. */
 int tdmix_server_add_generated_sample(tdmix_server* s, const double* params, int64_t n, uint64_t seed,
                                       uint32_t stream, int* sample_id);
 /* Queues an NLL + gradient evaluation of sample_id at params (host,

@@ -720,8 +720,9 @@ int tdmix_profile_read(tdmix_ctx* ctx, double* ms_out, int64_t* launches_out, in
   return TDMIX_OK;
 }
 
-int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t seed, uint32_t stream, int flat,
+int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t seed, uint32_t stream, int flags,
                    double* p_out, double* t_out, double* info) {
+  const bool flat = (flags & TDMIX_GEN_FLAT) != 0;
   if (!ctx || n < 1 || !p_out || (!flat && !params)) return fail(ctx, TDMIX_ERR_ARG, "bad argument");
   if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
   cudaGetLastError();  // a failure left by earlier, unrelated work must not be reported here
@@ -760,6 +761,7 @@ int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t see
   a.key0 = uint32_t(seed);
   a.key1 = uint32_t(seed >> 32);
   a.flat = flat ? 1 : 0;
+  a.prescreen = (flags & TDMIX_GEN_FP64_ONLY) ? 0 : 1;
   a.p_out = p_out;
   a.t_out = t_out;
   a.ld = n;
@@ -806,10 +808,14 @@ int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t see
   // headroom makes later batches exceed it and the sample be redrawn
   double env = 0, wmax = 0;
   cudaError_t e = cudaSuccess;
-  if (!flat) {
+  const int prescreen = a.prescreen;
+  if (!flat && info && info[0] > 0) {  // the caller's envelope (from an earlier call at the same parameters)
+    env = info[0];
+  } else if (!flat) {
     a.stream = stream ^ 0x80000000u;
     a.env = 0.0;
     a.cand0 = 0;
+    a.prescreen = 0;  // exact weights: the envelope is the same with and without the pre-screen
     if ((e = pass1(&wmax)) != cudaSuccess) {
       cleanup();
       return fail(ctx, TDMIX_ERR_CUDA, std::string("generator pilot: ") + cudaGetErrorString(e));
@@ -821,6 +827,7 @@ int tdmix_generate(tdmix_ctx* ctx, const double* params, int64_t n, uint64_t see
     env = 1.5 * wmax;
   }
   a.stream = stream;
+  a.prescreen = prescreen;
   int64_t have = 0, proposed = 0;
   int restarts = 0;
   while (have < n) {

@@ -175,6 +175,9 @@ struct tdmix_server {
   int next_sample = 0;
   bool stop = false;
   std::thread dispatcher, admitter;
+  // envelope of the generator at the last generating parameters (pilot once)
+  std::vector<double> env_params;
+  double env_value = 0;
   std::vector<double> latencies;
   double t_first = 0, t_last = 0;
   uint64_t n_done = 0, use_clock = 0;
@@ -409,6 +412,7 @@ void admitter_loop(tdmix_server* s) {
     // erased while admitting)
     const bool generated = rec.generated;
     const int64_t n = rec.n;
+    double gen_info[4] = {generated && rec.gen_params == s->env_params ? s->env_value : 0.0, 0, 0, 0};
     lk.unlock();
     void* cache = nullptr;
     int64_t tile_bytes = 0;
@@ -422,7 +426,7 @@ void admitter_loop(tdmix_server* s) {
           cudaMallocAsync(reinterpret_cast<void**>(&t), size_t(n) * sizeof(double), st) != cudaSuccess) {
         rc = TDMIX_ERR_NOMEM;
       } else {
-        rc = tdmix_generate(s->ctx, rec.gen_params.data(), n, rec.seed, rec.stream, 0, p, t, nullptr);
+        rc = tdmix_generate(s->ctx, rec.gen_params.data(), n, rec.seed, rec.stream, 0, p, t, gen_info);
         if (rc == TDMIX_OK) {
           tdmix_events ev{};
           ev.n = n;
@@ -448,6 +452,10 @@ void admitter_loop(tdmix_server* s) {
     std::string msg = rc ? internal::error_of(s->ctx) : std::string();
     lk.lock();
     rec.admitting = false;
+    if (generated && rc == TDMIX_OK) {
+      s->env_params = rec.gen_params;
+      s->env_value = gen_info[0];
+    }
     if (rc) {
       // every waiting request of this sample fails with the admission's status
       s->err = "admission: " + msg;

@@ -276,7 +276,8 @@ class TDMix:
         self._check(self._lib.tdmix_norm_matrix(self._ctx, out.ctypes.data))
         return (out[0::2] + 1j * out[1::2]).reshape(U, U)
 
-    def generate(self, n: int, seed: int, stream: int = 0, params=None, flat: bool = False, with_times: bool = True):
+    def generate(self, n: int, seed: int, stream: int = 0, params=None, flat: bool = False, with_times: bool = True,
+                 fp64_only: bool = False, envelope: float = 0.0):
         """n pseudo-events of the model at `params` (or flat phase space) on
         the GPU: (momenta (n, 4, 4) and times (n,) as CUDA float64 tensors,
         info dict)."""
@@ -287,8 +288,10 @@ class TDMix:
         p = None if flat else np.ascontiguousarray(np.asarray(params if params is not None else self.default_params(),
                                                              dtype=np.float64))
         info = np.zeros(4)
+        info[0] = envelope
+        flags = (1 if flat else 0) | (2 if fp64_only else 0)
         self._check(self._lib.tdmix_generate(self._ctx, None if p is None else p.ctypes.data, n, seed, stream,
-                                             int(flat), planes.data_ptr(), t.data_ptr() if t is not None else None,
+                                             flags, planes.data_ptr(), t.data_ptr() if t is not None else None,
                                              info.ctypes.data))
         p4 = planes.view(4, 4, n).permute(2, 0, 1)
         return p4, t, {"envelope": float(info[0]), "candidates": int(info[1]), "efficiency": float(info[2]),

@@ -120,3 +120,18 @@ def test_model_events_against_oracle(name, n_gen, n_ref):
     print(f"{name} t: chi2/dof {chi2:.1f}/{len(exp) - 1}, p = {p:.3f}")
     assert p > 1e-4
     assert t.min() >= 0
+
+
+def test_prescreen_gives_the_double_precision_sample():
+    """Weighing candidates in single precision first (with an error band,
+    the double-precision weight deciding inside it and for every candidate
+    that could be the largest weight) gives exactly the sample of weighing
+    every candidate in double precision."""
+    from paper_1702_06735_gb300.tdmix import TDMix
+    c = TDMix("d0_k3pi_full", "fp32")
+    par = c.default_params()
+    a, ta, ia = c.generate(40_000, seed=5, stream=2, params=par)
+    b, tb, ib = c.generate(40_000, seed=5, stream=2, params=par, fp64_only=True)
+    c.close()
+    assert ia["envelope"] == ib["envelope"] and ia["candidates"] == ib["candidates"]
+    assert torch.equal(a, b) and torch.equal(ta, tb)
