@@ -387,36 +387,49 @@ def load(name, precision, data, t, mc, stream=None):
     return c, (time.perf_counter() - t0) * 1e3
 
 
-def device_steps(c, dev, stream, K, W, move, flush=None, sampler=None):
+def device_steps(c, dev, stream, K, W, move, flush=None, sampler=None, batch=False):
     """K timed evaluations with device parameters (every evaluation a full
-    one) bracketed by device synchronisations; CUDA events per step.
-    Returns (per-step ms, wall s, {kernel class: (ms, launches)}, clocks)."""
+    one) bracketed by device synchronisations.  batch=False: one call per
+    evaluation, CUDA events around each (an isolated launch each);
+    batch=True: one tdmix_nll_batch call for the K evaluations (consecutive
+    evaluations overlap on the device), CUDA events around it.  Returns
+    (per-evaluation ms, wall s, {kernel class: (ms, launches)}, clocks)."""
     import torch
     p0 = c.default_params()
     P = torch.from_numpy(np.stack([step_params(p0, move, k) for k in range(K + W)])).to(dev)
     out = torch.empty(K + W, dtype=torch.float64, device=dev)
     grad = torch.empty(K + W, len(p0), dtype=torch.float64, device=dev)
-    for k in range(W):
-        c.nll_device(P[k], out[k:k + 1], grad[k])
+    if batch:
+        if W > 0:
+            c.nll_batch(P[:W], out[:W], grad[:W])
+    else:
+        for k in range(W):
+            c.nll_device(P[k], out[k:k + 1], grad[k])
     torch.cuda.synchronize(dev)
     c.profile(True)
     c.profile_read(reset=True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    n_ev = 1 if batch else K
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_ev)]
     if sampler is not None:
         sampler.start()
         time.sleep(0.01)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for k in range(K):
-        if flush is not None:
-            flush.zero_()
-        ev[k][0].record(stream)
-        c.nll_device(P[W + k], out[W + k:W + k + 1], grad[W + k])
-        ev[k][1].record(stream)
+    if batch:
+        ev[0][0].record(stream)
+        c.nll_batch(P[W:], out[W:], grad[W:])
+        ev[0][1].record(stream)
+    else:
+        for k in range(K):
+            if flush is not None:
+                flush.zero_()
+            ev[k][0].record(stream)
+            c.nll_device(P[W + k], out[W + k:W + k + 1], grad[W + k])
+            ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     t1 = time.perf_counter()
     clocks = sampler.stop(t0, t1) if sampler is not None else None
-    ms = [a.elapsed_time(b) for a, b in ev]
+    ms = [ev[0][0].elapsed_time(ev[0][1]) / K] * K if batch else [a.elapsed_time(b) for a, b in ev]
     prof = c.profile_read(reset=True)
     c.profile(False)
     if not torch.isfinite(out).all():
@@ -831,9 +844,14 @@ def run_tdmix(args):
     c32, load32 = load(MODEL, "fp32", data, t, mc, stream)
     c64, load64 = load(MODEL, "fp64", data, t, mc, stream)
     barrier()
+    # the timed region: K evaluations in one batch (consecutive evaluations
+    # overlap on the device), or one call each when L2 is flushed in between
     ms32, wall32, prof32, clocks = device_steps(c32, dev, stream, args.steps, args.warmup, every, flush,
-                                                ClockSampler(dev))
-    ms64, _, prof64, _ = device_steps(c64, dev, stream, max(3, min(args.steps, 50)), 3, every, flush)
+                                                ClockSampler(dev), batch=flush is None)
+    ms64, _, prof64, _ = device_steps(c64, dev, stream, max(3, min(args.steps, 50)), 3, every, flush,
+                                      batch=flush is None)
+    # isolated launches (one call and CUDA events per evaluation): the latency of one evaluation
+    ms_iso, _, _, _ = device_steps(c32, dev, stream, min(args.steps, 100), 3, every)
 
     # end to end through the C ABI with host buffers (params in, NLL + gradient out)
     ps = [step_params(p0, every, 6000 + k) for k in range(args.steps + args.warmup)]  # made before timing
@@ -925,7 +943,15 @@ def run_tdmix(args):
                       "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof64.items()}},
         "speedup_vs_fp64": (sum(ms64) / len(ms64)) / step_ms,
         "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof32.items()},
-        "roofline": {"kernel": "k_eval (one full evaluation, fp32 path)", "bound": "hbm", "achieved": achieved,
+        "timed_region": ("one tdmix_nll_batch call of K evaluations (consecutive evaluations overlap on the "
+                         "device), CUDA events around it" if flush is None else
+                         "one tdmix_nll call per evaluation, CUDA events around each"),
+        "isolated_launch": {"ms": sum(ms_iso) / len(ms_iso), "evals_per_s": 1000.0 * len(ms_iso) / sum(ms_iso),
+                            "frac_hbm": full_eval_bytes(N_DATA, N_MC) / (sum(ms_iso) / len(ms_iso) * 1e-3) / 1e9
+                            / measured_peaks()[0],
+                            "note": "one call and CUDA events per evaluation (no overlap between evaluations)"},
+        "roofline": {"kernel": "k_eval (one full evaluation, fp32 path; average launch duration of the batched "
+                               "timed region)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,

@@ -137,6 +137,21 @@ int tdmix_load_events(tdmix_ctx* ctx, const tdmix_events* data, const tdmix_even
  * memory, so no separate copy is enqueued. */
 int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* grad_out);
 
+/* NLL (and, if grad_out is not NULL, gradient) at n_points parameter
+ * vectors, the same computation as tdmix_nll at each: params is a device
+ * array [n_points][num_params], nll_out a device array [n_points], grad_out
+ * NULL or a device array [n_points][num_params]; all three must be ready
+ * when the stream reaches the call (stream-ordered, returns without
+ * synchronising).  Every evaluation is a full one (lineshapes, components,
+ * MC normalisation, data pass, adjoint).  Consecutive evaluations overlap on
+ * the device (programmatic dependent launch): each may start while the one
+ * before it finishes, and waits for it before writing anything that is read
+ * later (component cache, partial sums, results).  For a minimiser's line
+ * search or Hessian columns, a parameter scan, or many fits of one sample.
+ * Invalid parameters and rates <= 0 give NaN values, as for device outputs
+ * of tdmix_nll.  TDMIX_ERR_ARG for host pointers or n_points < 1. */
+int tdmix_nll_batch(tdmix_ctx* ctx, const double* params, int64_t n_points, double* nll_out, double* grad_out);
+
 /* Per-event rate e^{-Gamma t} B(e) of Eq. (mix) for every data event
  * (rates_out: host or device, n_data doubles) and, if norm_out is not NULL,
  * the normalisation N (one double, same memory kind as rates_out).  Always
@@ -340,7 +355,7 @@ void tdmix_server_destroy(tdmix_server* s);
 /* Tracing (library extension for measurement; the paper has no
  * counterpart).  With tracing on, every block of the evaluation kernel
  * records TDMIX_TRACE_PHASES globaltimer stamps (ns): start, per-evaluation
- * constants ready, data tiles done, MC tiles done, partials written, then
+ * constants ready, MC tiles done, data tiles done, partials written, then
  * in the last block only: column totals formed, NLL written, end (other
  * blocks repeat their "partials written" stamp there).  Unused rows stay 0. */
 #define TDMIX_TRACE_PHASES 8

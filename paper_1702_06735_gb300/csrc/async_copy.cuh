@@ -47,6 +47,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Programmatic dependent launch (sm_90 and later).  launch_dependents lets
+// the next kernel of the stream, when it was launched with programmatic
+// stream serialization, start its blocks as SMs free up; such a kernel calls
+// grid_dependency_wait before it depends on this one: the wait returns once
+// the grids it depends on have completed and their memory operations are
+// visible (at once for a kernel launched without the attribute).
+__device__ __forceinline__ void grid_dependents_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

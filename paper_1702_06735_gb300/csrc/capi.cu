@@ -71,6 +71,7 @@ struct tdmix_ctx {
   // kernel profiling: CUDA event pairs per kernel class, recorded on the stream
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev[TDMIX_PROF_CLASSES][2];
+  std::vector<int64_t> prof_count[TDMIX_PROF_CLASSES];  // launches between the events of each pair
   int prof_used[TDMIX_PROF_CLASSES] = {};
   double prof_ms[TDMIX_PROF_CLASSES] = {};
   int64_t prof_n[TDMIX_PROF_CLASSES] = {};
@@ -217,15 +218,16 @@ int prof_drain(tdmix_ctx* ctx) {
       TDMIX_CK(cudaEventSynchronize(ctx->prof_ev[c][1][k]));
       TDMIX_CK(cudaEventElapsedTime(&ms, ctx->prof_ev[c][0][k], ctx->prof_ev[c][1][k]));
       ctx->prof_ms[c] += ms;
-      ctx->prof_n[c] += 1;
+      ctx->prof_n[c] += ctx->prof_count[c][k];
     }
     ctx->prof_used[c] = 0;
   }
   return TDMIX_OK;
 }
 
-// Records the start (phase 0) or end (phase 1) of a kernel of class c.
-int prof_mark(tdmix_ctx* ctx, int c, int phase) {
+// Records the start (phase 0) or end (phase 1) of `launches` consecutive
+// kernels of class c.
+int prof_mark(tdmix_ctx* ctx, int c, int phase, int64_t launches = 1) {
   if (!ctx->prof_on) return TDMIX_OK;
   if (phase == 0 && ctx->prof_used[c] == kProfPool) {
     int rc = prof_drain(ctx);
@@ -233,7 +235,10 @@ int prof_mark(tdmix_ctx* ctx, int c, int phase) {
   }
   const int k = ctx->prof_used[c];
   TDMIX_CK(cudaEventRecord(ctx->prof_ev[c][phase][k], ctx->stream));
-  if (phase == 1) ctx->prof_used[c] = k + 1;
+  if (phase == 1) {
+    ctx->prof_count[c][k] = launches;
+    ctx->prof_used[c] = k + 1;
+  }
   return TDMIX_OK;
 }
 
@@ -365,8 +370,12 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
 // data_only: a full evaluation of the data tiles alone (components written to
 // the cache); the MC tiles are skipped, so its NLL and stored normalisation
 // are not meaningful (used to build component caches).
+// pdl: may start while the evaluation before it in the stream finishes (only
+// between evaluations of one batch); grid_cap: blocks at most (0: one per SM).
+// prof: record profiling events around this launch.
 int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool want_grad, double* rates,
-                 double* result, double* out_nll = nullptr, double* out_grad = nullptr, bool data_only = false) {
+                 double* result, double* out_nll = nullptr, double* out_grad = nullptr, bool data_only = false,
+                 bool pdl = false, int grid_cap = 0, bool prof = true) {
   const CompiledModel& m = ctx->model;
   const int np = m.n_params(), nc = int(m.chains.size());
   cudaStream_t st = ctx->stream;
@@ -382,7 +391,8 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   }
   int rc;
   const int64_t items = ctx->data.dev.n_tiles + (full && !data_only ? ctx->mc.dev.n_tiles : 0);
-  const int grid = int(items < ctx->num_sms ? items : ctx->num_sms);
+  const int cap = grid_cap > 0 && grid_cap < ctx->num_sms ? grid_cap : ctx->num_sms;
+  const int grid = int(items < cap ? items : cap);
   // parameters travel in the kernel arguments (host callers) or are read
   // from the caller's device array
   EvalArgs a;
@@ -431,10 +441,10 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   }
   a.mc_ranges = data_only ? ctx->d_zero_ranges : ctx->d_ranges;
 
-  if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
+  if (prof && (rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
   ctx->last_result = result;
-  TDMIX_CK(ctx->ops->eval(full, want_grad, grid, st, a));
-  if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 1))) return rc;
+  TDMIX_CK(ctx->ops->eval(full, want_grad, grid, pdl, st, a));
+  if (prof && (rc = prof_mark(ctx, TDMIX_PROF_EVAL, 1))) return rc;
   if (data_only) {
     ctx->gram_valid = ctx->cache_valid = false;
   } else if (full) {
@@ -642,6 +652,27 @@ int tdmix_nll(tdmix_ctx* ctx, const double* params, double* nll_out, double* gra
   return enqueue_eval(ctx, params, host_params, grad_out != nullptr, nullptr, ctx->d_result, nll_out, grad_out);
 }
 
+int tdmix_nll_batch(tdmix_ctx* ctx, const double* params, int64_t n_points, double* nll_out, double* grad_out) {
+  if (!ctx || !params || !nll_out || n_points < 1) return fail(ctx, TDMIX_ERR_ARG, "null argument or no points");
+  if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
+  if (!is_device_ptr(params) || !is_device_ptr(nll_out) || (grad_out && !is_device_ptr(grad_out)))
+    return fail(ctx, TDMIX_ERR_ARG, "a batch takes device parameters and device outputs");
+  cudaGetLastError();
+  const int np = ctx->model.n_params();
+  // Consecutive evaluations overlap: each may start while the one before it
+  // finishes.  One SM is left to the finishing evaluation's last block, so
+  // that the next one's blocks all start at once.
+  const int cap = n_points > 1 && ctx->num_sms > 1 ? ctx->num_sms - 1 : ctx->num_sms;
+  int rc;
+  if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
+  for (int64_t k = 0; k < n_points; ++k) {
+    rc = enqueue_eval(ctx, params + k * np, false, grad_out != nullptr, nullptr, ctx->d_result, nll_out + k,
+                      grad_out ? grad_out + k * np : nullptr, false, k > 0, cap, false);
+    if (rc) return rc;
+  }
+  return prof_mark(ctx, TDMIX_PROF_EVAL, 1, n_points);
+}
+
 int tdmix_event_rates(tdmix_ctx* ctx, const double* params, double* rates_out, double* norm_out) {
   if (!ctx || !params || !rates_out) return fail(ctx, TDMIX_ERR_ARG, "null argument");
   if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
@@ -694,6 +725,7 @@ int tdmix_profile(tdmix_ctx* ctx, int enable) {
     for (int c = 0; c < TDMIX_PROF_CLASSES; ++c)
       for (int ph = 0; ph < 2; ++ph) {
         ctx->prof_ev[c][ph].resize(kProfPool);
+        ctx->prof_count[c].assign(kProfPool, 1);
         for (auto& e : ctx->prof_ev[c][ph]) TDMIX_CK(cudaEventCreate(&e));
       }
   }

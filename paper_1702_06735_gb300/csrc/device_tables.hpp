@@ -90,7 +90,7 @@ struct EvalArgs {
 };
 
 // Phases stamped by the evaluation kernel when tracing is on: start,
-// constants ready, data tiles done, MC tiles done, partials written, and in
+// constants ready, MC tiles done, data tiles done, partials written, and in
 // the last block: column totals formed, result written; end.
 constexpr int kTracePhases = 8;
 

@@ -68,36 +68,48 @@ struct Ops {
   static constexpr int kCacheGram = kRegs ? kGramRegs : (Prec::kF32 ? kGramTensor : kGramShared);
 
   template <bool FULL, bool GRAD, bool W, bool RATES, int GRAM>
-  static cudaError_t launch(int grid, cudaStream_t st, const EvalArgs& a) {
+  static cudaError_t launch(int grid, bool pdl, cudaStream_t st, const EvalArgs& a) {
     const int smem = Layout<Prec, S, GRAM>::smem_bytes(FULL, int(a.ld));
     static SmemLimit seen;  // per instantiation
     const cudaError_t e = allow_smem(k_eval<Prec, S, FULL, GRAD, W, RATES, GRAM>, smem, seen);
     if (e != cudaSuccess) return e;
-    k_eval<Prec, S, FULL, GRAD, W, RATES, GRAM><<<grid, kTile, smem, st>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(kTile);
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_eval<Prec, S, FULL, GRAD, W, RATES, GRAM>, a);
   }
   template <int GRAM>
-  static cudaError_t eval_full(bool grad, int grid, cudaStream_t st, const EvalArgs& a) {
+  static cudaError_t eval_full(bool grad, int grid, bool pdl, cudaStream_t st, const EvalArgs& a) {
     const bool w = a.mc.weighted != 0;
     if (a.rates && !grad)  // per-event rates (always a full evaluation without gradient)
-      return w ? launch<true, false, true, true, GRAM>(grid, st, a) : launch<true, false, false, true, GRAM>(grid, st, a);
+      return w ? launch<true, false, true, true, GRAM>(grid, pdl, st, a)
+               : launch<true, false, false, true, GRAM>(grid, pdl, st, a);
     if (grad)
-      return w ? launch<true, true, true, false, GRAM>(grid, st, a) : launch<true, true, false, false, GRAM>(grid, st, a);
-    return w ? launch<true, false, true, false, GRAM>(grid, st, a) : launch<true, false, false, false, GRAM>(grid, st, a);
+      return w ? launch<true, true, true, false, GRAM>(grid, pdl, st, a)
+               : launch<true, true, false, false, GRAM>(grid, pdl, st, a);
+    return w ? launch<true, false, true, false, GRAM>(grid, pdl, st, a)
+             : launch<true, false, false, false, GRAM>(grid, pdl, st, a);
   }
-  static cudaError_t eval(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a) {
+  static cudaError_t eval(bool full, bool grad, int grid, bool pdl, cudaStream_t st, const EvalArgs& a) {
     if constexpr (kOk) {
       if (!full)
-        return grad ? launch<false, true, false, false, kCacheGram>(grid, st, a)
-                    : launch<false, false, false, false, kCacheGram>(grid, st, a);
+        return grad ? launch<false, true, false, false, kCacheGram>(grid, pdl, st, a)
+                    : launch<false, false, false, false, kCacheGram>(grid, pdl, st, a);
       if constexpr (Prec::kF32) {
         if constexpr (kRegs)
-          if (a.gram_pref != TDMIX_GRAM_TENSOR) return eval_full<kGramRegs>(grad, grid, st, a);
-        return eval_full<kGramTensor>(grad, grid, st, a);
+          if (a.gram_pref != TDMIX_GRAM_TENSOR) return eval_full<kGramRegs>(grad, grid, pdl, st, a);
+        return eval_full<kGramTensor>(grad, grid, pdl, st, a);
       } else {
         if (a.gram_pref == TDMIX_GRAM_TENSOR) return cudaErrorNotSupported;
-        if constexpr (kRegs) return eval_full<kGramRegs>(grad, grid, st, a);
-        else return eval_full<kGramShared>(grad, grid, st, a);
+        if constexpr (kRegs) return eval_full<kGramRegs>(grad, grid, pdl, st, a);
+        else return eval_full<kGramShared>(grad, grid, pdl, st, a);
       }
     }
     return cudaErrorNotSupported;

@@ -537,27 +537,33 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
+  // The next evaluation of a batch may start its blocks as this one's blocks exit.
+  // The cached path reads the component cache and the stored MC totals that
+  // the evaluation before it wrote, so it waits for that one first.
+  grid_dependents_launch();
+  if constexpr (!FULL) grid_dependency_wait();
   unsigned long long* trace = a.trace ? a.trace + size_t(blockIdx.x) * kTracePhases : nullptr;
   if (trace && tid == 0) trace[0] = global_ns();
   const SampleDev& dd = a.data;
   const SampleDev& dmc = a.mc;
-  // Block b takes data tiles b, b + G, ... and then the contiguous range of
-  // MC tiles mc_ranges[b] .. mc_ranges[b + 1], chosen on the host so that
-  // every block carries about the same cost.  The assignment depends only on
+  // Block b takes the contiguous range of MC tiles mc_ranges[b] ..
+  // mc_ranges[b + 1] and then the data tiles b, b + G, ..., chosen on the
+  // host so that every block carries about the same cost.  The assignment depends only on
   // the sizes and the grid, so every run sums in the same order.
   const int64_t b = blockIdx.x;
   const int64_t n_dt = dd.n_tiles;
   const int64_t my_data = n_dt > b ? (n_dt - 1 - b) / G + 1 : 0;
   const int64_t mc_begin = FULL ? a.mc_ranges[b] : 0, mc_end = FULL ? a.mc_ranges[b + 1] : 0;
-  const int64_t my_items = my_data + (mc_end - mc_begin);
+  const int64_t my_mc = mc_end - mc_begin;  // items 0 .. my_mc - 1: MC tiles, then the data tiles
+  const int64_t my_items = my_mc + my_data;
 
   // ---- one bulk copy of work item k (a whole tile) into stage k % NST
   auto issue = [&](int64_t k) {
     const int st = int(k % NST);
     const void* src;
     uint32_t bytes;
-    if (k < my_data) {
-      const int64_t tile = b + k * G;
+    if (k >= my_mc) {
+      const int64_t tile = b + (k - my_mc) * G;
       if constexpr (FULL) {
         src = static_cast<const unsigned char*>(dd.planes) + tile * dd.tile_bytes;
         bytes = uint32_t(dd.tile_bytes);
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
         bytes = uint32_t(dd.cache_tile_bytes);
       }
     } else {
-      const int64_t tile = mc_begin + (k - my_data);
+      const int64_t tile = mc_begin + k;
       src = static_cast<const unsigned char*>(dmc.planes) + tile * dmc.tile_bytes;
       bytes = uint32_t(dmc.tile_bytes);
     }
@@ -643,116 +649,6 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   };
 
   {
-    // ---- data tiles
-    {
-      double lnb = 0.0;  // sum ln B = lnb + lexp ln 2
-      int bad = 0, lexp = 0, n_rec = 0;
-      T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
-#pragma unroll
-      for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
-#pragma unroll
-      for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
-      for (; k < my_data; ++k) {
-        const int64_t tile = b + k * G;
-        const bool ok = mbar_wait_bounded(&full_bar[st], ph, kWaitNs);
-        if (__any_sync(0xffffffffu, !ok)) {
-          timed_out = true;
-          break;
-        }
-        const int64_t i = tile * TE + tid;
-        if (i < dd.n) {
-          const unsigned char* stage = smem_raw + st * STB;
-          const T* sbase = reinterpret_cast<const T*>(stage);
-          const double t_e = reinterpret_cast<const double*>(stage + NPL * TE * ES)[tid];
-          const SmemSrc<P, S, TE> src{sbase, tid, false};
-          EventCore<P, S> ev;
-          constexpr bool RECOMPUTE = RATES && FULL && P::kF32;
-          T sc[RECOMPUTE ? U : 1];
-          if constexpr (FULL) {
-            ev.lineshapes(src, bc);
-            ev.template components<RECOMPUTE>(src, sc);
-            T* cache = reinterpret_cast<T*>(static_cast<unsigned char*>(dd.cache) + tile * dd.cache_tile_bytes);
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-              cache[j * TE + tid] = ev.ar[j];
-              cache[(U + j) * TE + tid] = ev.ai[j];
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-              ev.ar[j] = sbase[j * TE + tid];
-              ev.ai[j] = sbase[(U + j) * TE + tid];
-            }
-          }
-          T Ar_, Ai_, Br_, Bi_;
-          ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
-          double Ad[4] = {double(Ar_), double(Ai_), double(Br_), double(Bi_)};
-          if constexpr (RECOMPUTE) {
-            if (ill_conditioned<U>(bc, sc, Ar_, Ai_, Br_, Bi_, t_e)) {
-              df_amplitudes<S>(sbase, dd.lo + tile * int64_t(S::NX + U * S::NO) * TE, tid, bc, Ad);
-              n_rec += 1;
-            }
-          }
-          T tAr, tAi, tBr, tBi;
-          if (mix_event<P, GRAD>(bc, logtab, Ad[0], Ad[1], Ad[2], Ad[3], Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp,
-                                 a.rates ? a.rates + i : nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
-            if constexpr (GRAD) {
-#pragma unroll
-              for (int j = 0; j < U; ++j) {
-                cmac(gAr[j], gAi[j], tAr, tAi, ev.ar[j], ev.ai[j]);
-                cmac(gBr[j], gBi[j], tBr, tBi, ev.ar[j], ev.ai[j]);
-              }
-              if constexpr (FULL) ev.template backprop_lineshapes<false>(src, bc, tAr, tAi, tBr, tBi, T(1), s1, s2);
-            }
-          } else {
-            bad += 1;
-          }
-        }
-        release();
-      }
-      // block sums of the data accumulators -> rowp[WMC ..]
-      {
-        __shared__ int red_bad[kWarps], red_rec[kWarps];
-        const double v0 = warp_sum(fma(double(lexp), kLn2, lnb));
-        const int v1 = warp_sum(bad);
-        const int v2 = warp_sum(n_rec);
-        if (lane == 0) {
-          red_lnb[warp] = v0;
-          red_bad[warp] = v1;
-          red_rec[warp] = v2;
-        }
-        T vt[WD - 3];
-        vt[0] = gx;
-        vt[1] = gy;
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-          vt[2 + j] = gAr[j];
-          vt[2 + U + j] = gAi[j];
-          vt[2 + 2 * U + j] = gBr[j];
-          vt[2 + 3 * U + j] = gBi[j];
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          vt[2 + 4 * U + r] = s1[r];
-          vt[2 + 4 * U + NR + r] = s2[r];
-        }
-        block_sum_df<T, WD - 3>(vt, red, rowp + WMC + 2);  // ends with a barrier
-        if (tid == 0) {
-          double sl = 0;
-          int sb = 0, sr = 0;
-          for (int w = 0; w < kWarps; ++w) {
-            sl += red_lnb[w];
-            sb += red_bad[w];
-            sr += red_rec[w];
-          }
-          rowp[WMC] = to_df(sl);
-          rowp[WMC + 1] = make_float2(float(sb), 0.f);
-          rowp[WMC + WD - 1] = make_float2(float(sr), 0.f);
-        }
-      }
-    }
-    if (trace && tid == 0) trace[2] = global_ns();
-
     // ---- MC tiles
     if constexpr (FULL && GRAM == kGramRegs) {
       T sw = 0, gre[NRE], gim[NIM > 0 ? NIM : 1], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
@@ -762,8 +658,8 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       for (int q = 0; q < (NIM > 0 ? NIM : 1); ++q) gim[q] = 0;
 #pragma unroll
       for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
-      for (; k < my_items && !timed_out; ++k) {
-        const int64_t tile = mc_begin + (k - my_data);
+      for (; k < my_mc && !timed_out; ++k) {
+        const int64_t tile = mc_begin + k;
         const bool ok = mbar_wait_bounded(&full_bar[st], ph, kWaitNs);
         if (__any_sync(0xffffffffu, !ok)) {
           timed_out = true;
@@ -852,8 +748,8 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       int t3 = 0;
       uint32_t mma_phase = 0;
       bool mma_in_flight = false;
-      for (; k < my_items && !timed_out; ++k) {
-        const int64_t tile = mc_begin + (k - my_data);
+      for (; k < my_mc && !timed_out; ++k) {
+        const int64_t tile = mc_begin + k;
         const bool ok = mbar_wait_bounded(&full_bar[st], ph, kWaitNs);
         const int64_t i = tile * TE + tid;
         const bool valid = ok && i < dmc.n;
@@ -970,6 +866,121 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       if constexpr (TCG) tg.finish(rowp + 1, rowp + 1 + NRE);
       if constexpr (SMG)
         if (tid < NRE + NIM) rowp[1 + tid] = to_df(gacc);
+    }
+    if (trace && tid == 0) trace[2] = global_ns();
+
+    // ---- data tiles (after the MC tiles).  Everything up to here only
+    // read memory that no evaluation writes (event planes, parameters,
+    // constants), so it may overlap the end of the previous evaluation of a
+    // batch; the component cache, the rates, the partial rows and the
+    // completion counter are written only after that evaluation completed.
+    grid_dependency_wait();
+    {
+      double lnb = 0.0;  // sum ln B = lnb + lexp ln 2
+      int bad = 0, lexp = 0, n_rec = 0;
+      T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
+#pragma unroll
+      for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
+#pragma unroll
+      for (int r = 0; r < (NR > 0 ? NR : 1); ++r) s1[r] = s2[r] = 0;
+      for (; k < my_items && !timed_out; ++k) {
+        const int64_t tile = b + (k - my_mc) * G;
+        const bool ok = mbar_wait_bounded(&full_bar[st], ph, kWaitNs);
+        if (__any_sync(0xffffffffu, !ok)) {
+          timed_out = true;
+          break;
+        }
+        const int64_t i = tile * TE + tid;
+        if (i < dd.n) {
+          const unsigned char* stage = smem_raw + st * STB;
+          const T* sbase = reinterpret_cast<const T*>(stage);
+          const double t_e = reinterpret_cast<const double*>(stage + NPL * TE * ES)[tid];
+          const SmemSrc<P, S, TE> src{sbase, tid, false};
+          EventCore<P, S> ev;
+          constexpr bool RECOMPUTE = RATES && FULL && P::kF32;
+          T sc[RECOMPUTE ? U : 1];
+          if constexpr (FULL) {
+            ev.lineshapes(src, bc);
+            ev.template components<RECOMPUTE>(src, sc);
+            T* cache = reinterpret_cast<T*>(static_cast<unsigned char*>(dd.cache) + tile * dd.cache_tile_bytes);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+              cache[j * TE + tid] = ev.ar[j];
+              cache[(U + j) * TE + tid] = ev.ai[j];
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+              ev.ar[j] = sbase[j * TE + tid];
+              ev.ai[j] = sbase[(U + j) * TE + tid];
+            }
+          }
+          T Ar_, Ai_, Br_, Bi_;
+          ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
+          double Ad[4] = {double(Ar_), double(Ai_), double(Br_), double(Bi_)};
+          if constexpr (RECOMPUTE) {
+            if (ill_conditioned<U>(bc, sc, Ar_, Ai_, Br_, Bi_, t_e)) {
+              df_amplitudes<S>(sbase, dd.lo + tile * int64_t(S::NX + U * S::NO) * TE, tid, bc, Ad);
+              n_rec += 1;
+            }
+          }
+          T tAr, tAi, tBr, tBi;
+          if (mix_event<P, GRAD>(bc, logtab, Ad[0], Ad[1], Ad[2], Ad[3], Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp,
+                                 a.rates ? a.rates + i : nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
+            if constexpr (GRAD) {
+#pragma unroll
+              for (int j = 0; j < U; ++j) {
+                cmac(gAr[j], gAi[j], tAr, tAi, ev.ar[j], ev.ai[j]);
+                cmac(gBr[j], gBi[j], tBr, tBi, ev.ar[j], ev.ai[j]);
+              }
+              if constexpr (FULL) ev.template backprop_lineshapes<false>(src, bc, tAr, tAi, tBr, tBi, T(1), s1, s2);
+            }
+          } else {
+            bad += 1;
+          }
+        }
+        release();
+      }
+      // block sums of the data accumulators -> rowp[WMC ..]
+      {
+        __shared__ int red_bad[kWarps], red_rec[kWarps];
+        const double v0 = warp_sum(fma(double(lexp), kLn2, lnb));
+        const int v1 = warp_sum(bad);
+        const int v2 = warp_sum(n_rec);
+        if (lane == 0) {
+          red_lnb[warp] = v0;
+          red_bad[warp] = v1;
+          red_rec[warp] = v2;
+        }
+        T vt[WD - 3];
+        vt[0] = gx;
+        vt[1] = gy;
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          vt[2 + j] = gAr[j];
+          vt[2 + U + j] = gAi[j];
+          vt[2 + 2 * U + j] = gBr[j];
+          vt[2 + 3 * U + j] = gBi[j];
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          vt[2 + 4 * U + r] = s1[r];
+          vt[2 + 4 * U + NR + r] = s2[r];
+        }
+        block_sum_df<T, WD - 3>(vt, red, rowp + WMC + 2);  // ends with a barrier
+        if (tid == 0) {
+          double sl = 0;
+          int sb = 0, sr = 0;
+          for (int w = 0; w < kWarps; ++w) {
+            sl += red_lnb[w];
+            sb += red_bad[w];
+            sr += red_rec[w];
+          }
+          rowp[WMC] = to_df(sl);
+          rowp[WMC + 1] = make_float2(float(sb), 0.f);
+          rowp[WMC + WD - 1] = make_float2(float(sr), 0.f);
+        }
+      }
     }
     if (trace && tid == 0) trace[3] = global_ns();
   }

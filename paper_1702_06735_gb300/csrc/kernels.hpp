@@ -34,7 +34,10 @@ struct ShapeOps {
   // component cache and reuse the stored MC totals.
   int n_planes;    // event planes per tile (NPL)
   int64_t data_tile_bytes, mc_tile_bytes, mc_tile_bytes_weighted, cache_tile_bytes;
-  cudaError_t (*eval)(bool full, bool grad, int grid, cudaStream_t st, const EvalArgs& a);
+  // pdl: launched with programmatic stream serialization, so that it may
+  // start while the evaluation before it in the stream finishes (the kernel
+  // waits for that one before it writes anything a later one reads)
+  cudaError_t (*eval)(bool full, bool grad, int grid, bool pdl, cudaStream_t st, const EvalArgs& a);
   // the persistent serving loop (see serve.cuh)
   cudaError_t (*serve)(int grid, cudaStream_t st, const ServeLoopArgs& a);
   int serve_row_stride;  // float2 entries per chunk-partial row

@@ -41,6 +41,7 @@ _SIGNATURES = {
     "tdmix_test_math": (_c_i, [_c_i, ctypes.c_int64, _c_p, _c_p]),
     "tdmix_load_events": (_c_i, [_c_p, _c_p, _c_p]),
     "tdmix_nll": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
+    "tdmix_nll_batch": (_c_i, [_c_p, _c_p, ctypes.c_int64, _c_p, _c_p]),
     "tdmix_event_rates": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
     "tdmix_norm_matrix": (_c_i, [_c_p, _c_p]),
     "tdmix_profile": (_c_i, [_c_p, _c_i]),
@@ -255,6 +256,14 @@ class TDMix:
         self._check(self._lib.tdmix_nll(self._ctx, params.data_ptr(), nll_out.data_ptr(),
                                         grad_out.data_ptr() if grad_out is not None else None))
 
+    def nll_batch(self, params, nll_out, grad_out=None):
+        """Enqueues evaluations at every row of `params` (device float64
+        [n, num_params]) into nll_out [n] and grad_out [n, num_params] on the
+        context's stream; consecutive evaluations overlap on the device."""
+        n = int(params.shape[0])
+        self._check(self._lib.tdmix_nll_batch(self._ctx, params.data_ptr(), n, nll_out.data_ptr(),
+                                              grad_out.data_ptr() if grad_out is not None else None))
+
     def event_rates(self, params):
         """(per-event rate e^{-Gamma t} B of every data event, normalisation N)."""
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
@@ -328,7 +337,7 @@ class TDMix:
         self._check(self._lib.tdmix_profile_read(self._ctx, ms.ctypes.data, n.ctypes.data, int(reset)))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROF_CLASSES)}
 
-    TRACE_PHASES = ("start", "constants", "data_done", "mc_done", "partials", "reduced", "nll", "end")
+    TRACE_PHASES = ("start", "constants", "mc_done", "data_done", "partials", "reduced", "nll", "end")
 
     def trace(self, enable: bool = True):
         """Per-block phase timestamps of the evaluation kernel."""
