@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--toys", type=int, default=1000, help="pseudo-experiments of the fp32 toy study (0: skip)")
     ap.add_argument("--toys-fp64", type=int, default=200, help="the first toys of the study run again on fp64")
     ap.add_argument("--sensitivity", type=int, default=100, help="toys per sample size of the sensitivity study")
+    ap.add_argument("--cached-only", type=int, default=0, metavar="N",
+                    help="only the cached data pass of the 16-chain model at N events (profiling runs)")
     ap.add_argument("--flush-l2", action="store_true",
                     help="write 256 MB between timed steps (default: none; the inputs of one evaluation exceed L2)")
     return ap.parse_args()
@@ -664,6 +666,7 @@ def config3_precision(dev, stream, peak):
     c.nll(p0)
     v_c, k_c, _ = host_steps(c, 50, 5, coef_xy)
     cb = cached_eval_bytes(len(t), c.n_components, 4)
+    fl[:] = 0
     fl[every] = 1
     c.set_floating(fl)
     ms, _, _, _ = device_steps(c, dev, stream, 5, 2, every)
@@ -678,6 +681,35 @@ def config3_precision(dev, stream, peak):
     del data, t, mc
     torch.cuda.empty_cache()
     return out
+
+
+def cached_pass(dev, stream, n_events, peak, steps=20):
+    """The cached data pass (coefficients and x, y moved; component cache
+    and stored normalisation reused) of the 16-chain model at n_events
+    generated events, fp32 path: kernel time per evaluation and its
+    algorithmic bytes against the HBM roofline."""
+    import torch
+    from paper_1702_06735_gb300.tdmix import TDMix
+    g = TDMix(MODEL, "fp64")
+    p0 = g.default_params()
+    data, t, _ = generate(g, n_events, 3, 10, params=p0)
+    mc, _, _ = generate(g, 100_000, 3, 11, flat=True, with_times=False)
+    g.close()
+    nc, nr = model_sizes(MODEL)
+    _, coef_xy, _ = class_masks(len(p0), nc, nr)
+    c, load_ms = load(MODEL, "fp32", data, t, mc, stream)
+    fl = np.zeros(len(p0), dtype=np.int32)
+    fl[coef_xy] = 1
+    c.set_floating(fl)
+    c.nll(p0)
+    v, k_ms, n = host_steps(c, steps, 3, coef_xy)
+    cb = cached_eval_bytes(n_events, c.n_components, 4)
+    c.close()
+    del data, t, mc
+    torch.cuda.empty_cache()
+    return {"events": n_events, "kernel_us": 1e3 * k_ms, "launches": n, "algorithmic_bytes": cb,
+            "achieved_gbs": cb / (k_ms * 1e-3) / 1e9, "frac_hbm": cb / (k_ms * 1e-3) / 1e9 / peak,
+            "evals_per_s_host_calls": v}
 
 
 def config4_gradient_fit(dev, stream):
@@ -824,6 +856,11 @@ def run_tdmix(args):
 
     stream = torch.cuda.current_stream(dev)
     nc, nr = model_sizes(MODEL)
+    if args.cached_only > 0:
+        if rank == 0:
+            print(json.dumps({"cached_pass": cached_pass(dev, stream, args.cached_only, measured_peaks()[0])}),
+                  flush=True)
+        return 0
 
     def barrier():
         if world > 1:

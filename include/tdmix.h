@@ -246,7 +246,8 @@ int tdmix_test_withhold_copy(tdmix_ctx* ctx, int enable);
  * functions (library extension for testing; the paper has no counterpart).
  * Evaluates routine `which` on n host arguments `in` on the current device
  * and writes n results to `out` (host; 4n for the mixing-series codes:
- * cosh v, sinh v, cos v, sin v per argument).  Returns TDMIX_ERR_ARG for a
+ * cosh v, sinh v, cos v, sin v per argument).  The Eq. (mix) codes take n
+ * records of 8 doubles in `in` and write 4 doubles per record.  Returns TDMIX_ERR_ARG for a
  * bad code, n < 1 or a null pointer, TDMIX_ERR_NOMEM / TDMIX_ERR_CUDA on
  * failure of its own allocations, copies or launch. */
 enum {
@@ -260,7 +261,13 @@ enum {
   TDMIX_MATH_MIX_TIER0 = 7, /* cosh, sinh, cos, sin by the series through z^3 (|v| <= 0.02) */
   TDMIX_MATH_MIX_TIER1 = 8, /* the same through z^5 (|v| <= 0.1) */
   TDMIX_MATH_MIX_TIER2 = 9, /* CUDA's cosh, sinh, cos, sin, for comparison */
-  TDMIX_MATH_CODES = 10
+  TDMIX_MATH_LOG_DF = 10,   /* ln v by the double-float table method of the fp32 path (v split into two
+                               floats; NaN outside its range) */
+  TDMIX_MATH_MIX_DF = 11,   /* Eq. (mix) of the fp32 path in double-float arithmetic: per record
+                               {Ar, Ai, Br, Bi, t, x, y, Gamma} (8 input doubles; amplitudes rounded to
+                               float, t to a double-float pair) out {ln B, e^{-Gamma t} B, ok, 0} */
+  TDMIX_MATH_MIX_F64 = 12,  /* the same records through the fp64 path's Eq. (mix), for comparison */
+  TDMIX_MATH_CODES = 13
 };
 int tdmix_test_math(int which, int64_t n, const double* in, double* out);
 

@@ -8,9 +8,10 @@
 // Hida, Li and Bailey (QD library, 2001), which keeps its relative accuracy
 // when the operands cancel, and multiplication the product with the
 // FMA-based TwoProd of the leading parts.
-// Used where a single-precision result would lose too much to cancellation
-// and the double-precision pipe of this GPU (about 1/64 of the FP32 rate)
-// would cost more: the recomputation of ill-conditioned data events.
+// Used where a single-precision result would lose too much and the
+// double-precision pipe of this GPU (about 1/64 of the FP32 rate) would cost
+// more: Eq. (mix) and ln B of the fp32 path's data events, and the
+// recomputation of ill-conditioned ones.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -43,6 +44,23 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   s = df_fast_two_sum(s.hi, s.lo);
   s.lo += t.lo;
   return df_fast_two_sum(s.hi, s.lo);
+}
+
+// Sum whose error is bounded by about 2^-48 (|a| + |b|) rather than by the
+// size of the result (the "sloppy" double-double sum): enough where the
+// accuracy is wanted relative to the operands, as in the mixing formula.
+__device__ __forceinline__ DF df_add_s(DF a, DF b) {
+  DF s = df_two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ DF df_sub_s(DF a, DF b) { return df_add_s(a, DF{-b.hi, -b.lo}); }
+
+// A double as a double-float (48 of its 53 bits).
+__device__ __forceinline__ DF df_from_double(double v) {
+  const float hi = float(v);
+  return DF{hi, float(v - double(hi))};
 }
 
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }

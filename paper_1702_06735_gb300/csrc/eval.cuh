@@ -79,6 +79,7 @@ struct BlockConst {
   double x, y, gamma;
   double hx, hy;                       // x Gamma / 2, y Gamma / 2
   float xf, yf, gammaf;                // fp32 copies for the fp32 adjoint
+  float hxh, hxl, hyh, hyl;            // x Gamma / 2 and y Gamma / 2 as double-float pairs (fp32 path)
   unsigned long long tlim[2];          // bit patterns of the decay times below which
                                        // |x|, |y| Gamma t / 2 <= 0.02 (resp. 0.1)
 };
@@ -340,6 +341,27 @@ struct EventCore {
   }
 };
 
+// Sensitivities of ln B = ln 2|Z|^2, Z = cosh(w) A - sinh(w) Abar, with
+// cosh w = cr + i ci and sinh w = sr + i si: d ln B = 2 Re(V dZ), V = 1/Z,
+// dZ = cosh(w) dA - sinh(w) dAbar + (sinh(w) A - cosh(w) Abar) dw, dw/dy =
+// Gamma t / 2, dw/dx = i Gamma t / 2 (tg = Gamma t).  Writes tA = V cosh(w),
+// tB = -V sinh(w) and adds d ln B / dy, d ln B / dx to gy, gx.
+template <class T>
+__device__ __forceinline__ void mix_adjoint(T cr, T ci, T sr, T si, T Zr, T Zi, T Ar, T Ai, T Br, T Bi, T tg, T& tAr,
+                                            T& tAi, T& tBr, T& tBi, T& gx, T& gy) {
+  const T iz = rcp<T>(fma(Zr, Zr, Zi * Zi));
+  const T Vr = Zr * iz, Vi = -Zi * iz;
+  tAr = fma(Vr, cr, -Vi * ci);
+  tAi = fma(Vr, ci, Vi * cr);
+  tBr = -fma(Vr, sr, -Vi * si);
+  tBi = -fma(Vr, si, Vi * sr);
+  T Dr = 0, Di = 0;
+  cmac(Dr, Di, sr, si, Ar, Ai);
+  cmac(Dr, Di, -cr, -ci, Br, Bi);
+  gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
+  gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
+}
+
 // One data event's rate from its amplitudes A, Abar and decay time: Eq. (mix) as B = 2 |cosh(w) A - sinh(w) Abar|^2 with
 // w = (y + i x) Gamma t / 2, in double precision.  For a B that is positive
 // and finite, adds ln B to the pair (lnb, lexp) as lnb + lexp ln 2 and
@@ -378,33 +400,141 @@ __device__ __forceinline__ bool mix_event(const BlockConst<typename P::T>& bc, c
   lnb += log_table_split(z2, logtab, e);
   lexp += e + 1;
   if constexpr (GRAD) {
-    T cr, ci, sr, si, Zrt, Zit, tg;
     if constexpr (P::kF32) {
-      const float tf = float(t_e);
-      tg = bc.gammaf * tf;
+      const float tg = bc.gammaf * float(t_e);
       float chf, shf, cbf, sbf;
       mixing_trig_f32(0.5f * bc.yf * tg, 0.5f * bc.xf * tg, chf, shf, cbf, sbf);
-      cr = chf * cbf; ci = shf * sbf; sr = shf * cbf; si = chf * sbf;
-      Zrt = 0; Zit = 0;
+      const float cr = chf * cbf, ci = shf * sbf, sr = shf * cbf, si = chf * sbf;
+      float Zrt = 0, Zit = 0;
       cmac(Zrt, Zit, cr, ci, Ar_, Ai_);
       cmac(Zrt, Zit, -sr, -si, Br_, Bi_);
+      mix_adjoint<T>(cr, ci, sr, si, Zrt, Zit, Ar_, Ai_, Br_, Bi_, tg, tAr, tAi, tBr, tBi, gx, gy);
     } else {
-      cr = chr; ci = chi; sr = shr; si = shi;
-      Zrt = Zr; Zit = Zi;
-      tg = gt;
+      mix_adjoint<T>(chr, chi, shr, shi, Zr, Zi, Ar_, Ai_, Br_, Bi_, gt, tAr, tAi, tBr, tBi, gx, gy);
     }
-    const T iz = rcp<T>(fma(Zrt, Zrt, Zit * Zit));
-    const T Vr = Zrt * iz, Vi = -Zit * iz;
-    tAr = fma(Vr, cr, -Vi * ci);
-    tAi = fma(Vr, ci, Vi * cr);
-    tBr = -fma(Vr, sr, -Vi * si);
-    tBi = -fma(Vr, si, Vi * sr);
-    T Dr = 0, Di = 0;
-    cmac(Dr, Di, sr, si, Ar_, Ai_);
-    cmac(Dr, Di, -cr, -ci, Br_, Bi_);
-    gy = fma(tg, fma(Vr, Dr, -Vi * Di), gy);
-    gx = fma(-tg, fma(Vr, Di, Vi * Dr), gx);
   }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (mix) of the fp32 path in double-float arithmetic.
+//
+// GB300 runs double-precision arithmetic at about 1/64 of the FP32 rate, so
+// the ~45 fp64 operations per event of mix_event bound the data pass by the
+// FP64 pipe, far below the memory rate at which its inputs arrive.  Here the
+// same quantities are formed from float pairs (value = hi + lo, about 48
+// significant bits) on the FP32 pipe: the mixing arguments a = y Gamma t / 2,
+// b = x Gamma t / 2 from the decay time and the constants as pairs; for
+// |a|, |b| <= 0.1 the Maclaurin series of cosh, sinh, cos, sin with their
+// leading terms in pairs and the tails (below 4e-4 relative) in floats;
+//   P = cosh a cos b - 1,  Q = sinh a sin b,  R = sinh a cos b,  S = cosh a sin b,
+// so that cosh w = 1 + P + i Q and sinh w = R + i S;
+//   Z = A + (P + i Q) A - (R + i S) Abar,  B = 2 |Z|^2,
+// with every product and sum in pairs (errors about 2^-48 of the operands'
+// magnitudes, as fp64's 2^-53); ln |Z|^2 by Tang's table method with the
+// table entries, the reduced argument and the leading series terms in pairs.
+// The mixing factors are within ~1e-15 of their values for |a|, |b| <= 0.02
+// (decay times below ~6.5 lifetimes at percent-level x, y) and ~1e-12 up to
+// 0.1; ln B within ~1e-15 absolute of ln of the computed B.  Larger
+// arguments (and B that is not a normal float) take mix_event.
+// ---------------------------------------------------------------------------
+
+// 1/6 as a double-float pair.
+constexpr float kSixthHi = 1.0f / 6.0f;
+constexpr float kSixthLo = float(1.0 / 6.0 - double(1.0f / 6.0f));
+
+// The four mixing factors P, Q, R, S for |a.hi|, |b.hi| <= 0.1.
+__device__ __forceinline__ void mixing_factors_df(DF a, DF b, DF& Pm, DF& Q, DF& R, DF& S) {
+  const DF a2 = df_mul(a, a), b2 = df_mul(b, b);
+  const float za = a2.hi, zb = b2.hi;
+  // cosh a - 1 = a^2 (1/2 + ta), 1 - cos b = b^2 (1/2 - tb); series through
+  // z^5 (first omitted term below 2e-21 relative at |a|, |b| = 0.1)
+  const float ta = za * (1.0f / 24 + za * (1.0f / 720 + za * (1.0f / 40320 + za * (1.0f / 3628800))));
+  const float tb = zb * (1.0f / 24 - zb * (1.0f / 720 - zb * (1.0f / 40320 - zb * (1.0f / 3628800))));
+  const DF Ca = df_mul(a2, df_fast_two_sum(0.5f, ta));
+  const DF Cb = df_mul(b2, df_fast_two_sum(0.5f, -tb));
+  // sinh a - a = a a^2 (1/6 + sa), b - sin b = b b^2 (1/6 - sb)
+  const float sa = za * (1.0f / 120 + za * (1.0f / 5040 + za * (1.0f / 362880 + za * (1.0f / 39916800))));
+  const float sb = zb * (1.0f / 120 - zb * (1.0f / 5040 - zb * (1.0f / 362880 - zb * (1.0f / 39916800))));
+  const DF Sa = df_mul(df_mul(a, a2), df_add_s(DF{kSixthHi, kSixthLo}, DF{sa, 0.0f}));
+  const DF Sb = df_mul(df_mul(b, b2), df_add_s(DF{kSixthHi, kSixthLo}, DF{-sb, 0.0f}));
+  const DF sha = df_add_s(a, Sa), snb = df_sub_s(b, Sb);  // sinh a, sin b
+  Pm = df_sub_s(df_sub_s(Ca, Cb), df_mul(Ca, Cb));
+  Q = df_mul(sha, snb);
+  R = df_sub_s(sha, df_mul(sha, Cb));
+  S = df_add_s(snb, df_mul(snb, Ca));
+}
+
+// ln v = e ln 2 + l for a double-float v whose hi part is a positive float
+// with exponent in [-100, 125] (returns false otherwise: below 2^-100 the lo
+// part of a pair can be subnormal and carry fewer bits).  v = 2^e m,
+// m in [1, 2); F = 1 + j/128 the grid point nearest m (m - F exact),
+// r = (m - F) / F with |r| <= 2^-8 (the pair 1/F from the table), then
+// ln v = e ln 2 + ln F + ln(1 + r), ln(1 + r) = r - r^2/2 (pairs) +
+// r^3 (1/3 - r/4 + r^2/5 - r^3/6 + r^4/7) (float; first omitted term below
+// 2^-67).  tab[j] = {1/F hi, lo, ln F hi, lo}.
+__device__ __forceinline__ bool log_df(DF v, const float4* tab, int& e, DF& l) {
+  const unsigned bits = __float_as_uint(v.hi);
+  const unsigned be = bits >> 23;                      // sign and biased exponent
+  if (be < 27u || be > 252u) return false;             // not positive, or exponent outside [-100, 125]
+  e = int(be) - 127;
+  const unsigned frac = bits & 0x007FFFFFu;
+  const float mh = __uint_as_float(frac | 0x3F800000u);
+  const float ml = v.lo * __uint_as_float(unsigned(127 - e) << 23);  // lo scaled by 2^-e (exact)
+  const unsigned j = (frac + (1u << 15)) >> 16;        // nearest multiple of 1/128, 0 .. 128
+  const float F = __uint_as_float(0x3F800000u + (j << 16));
+  const float4 t = tab[j];
+  const DF r = df_mul(df_two_sum(mh - F, ml), DF{t.x, t.y});
+  const DF r2 = df_mul(r, r);
+  const float rh = r.hi;
+  const float c = rh * rh * rh * (1.0f / 3 + rh * (-0.25f + rh * (0.2f + rh * (-1.0f / 6 + rh * (1.0f / 7)))));
+  const DF l1 = df_add_s(df_add_s(r, DF{-0.5f * r2.hi, -0.5f * r2.lo}), DF{c, 0.0f});
+  l = df_add_s(DF{t.z, t.w}, l1);
+  return true;
+}
+
+// The fp32 path's counterpart of mix_event<PrecF32, GRAD>: A, Abar as
+// double-float pairs (lo parts zero unless the event was recomputed), the
+// decay time as a pair (th, tl); ln B is added to the pair (lnb, lexp) as
+// lnb + lexp ln 2 with lnb a double-float accumulator.  The sensitivities
+// are formed in fp32 from the leading parts of the mixing factors and Z.
+template <bool GRAD>
+__device__ __forceinline__ bool mix_event_df(const BlockConst<float>& bc, const double2* logtab, const float4* logtab_f,
+                                             DF Ar, DF Ai, DF Br, DF Bi, float th, float tl, DF& lnb, int& lexp,
+                                             double* rate, float& tAr, float& tAi, float& tBr, float& tBi, float& gx,
+                                             float& gy) {
+  const DF t{th, tl};
+  const DF a = df_mul(DF{bc.hyh, bc.hyl}, t), b = df_mul(DF{bc.hxh, bc.hxl}, t);
+  if (!(fabsf(a.hi) <= 0.1f && fabsf(b.hi) <= 0.1f)) {  // long decay times, or t not finite
+    double l = 0.0;
+    const bool ok = mix_event<PrecF32, GRAD>(bc, logtab, df_to_double(Ar), df_to_double(Ai), df_to_double(Br),
+                                             df_to_double(Bi), Ar.hi, Ai.hi, Br.hi, Bi.hi, df_to_double(t), l, lexp,
+                                             rate, tAr, tAi, tBr, tBi, gx, gy);
+    lnb = df_add_s(lnb, df_from_double(l));
+    return ok;
+  }
+  DF Pm, Q, R, S;
+  mixing_factors_df(a, b, Pm, Q, R, S);
+  const DF Zr = df_add_s(Ar, df_sub_s(df_sub_s(df_mul(Pm, Ar), df_mul(Q, Ai)), df_sub_s(df_mul(R, Br), df_mul(S, Bi))));
+  const DF Zi = df_add_s(Ai, df_sub_s(df_add_s(df_mul(Pm, Ai), df_mul(Q, Ar)), df_add_s(df_mul(R, Bi), df_mul(S, Br))));
+  const DF z2 = df_add_s(df_mul(Zr, Zr), df_mul(Zi, Zi));  // B = 2 z2
+  if (rate) *rate = exp(-bc.gamma * df_to_double(t)) * (2.0 * df_to_double(z2));
+  int e;
+  DF l;
+  if (log_df(z2, logtab_f, e, l)) {
+    lnb = df_add_s(lnb, l);
+    lexp += e + 1;
+  } else {
+    // B <= 0, not finite, or outside the float exponent range: double precision
+    const double v = df_to_double(z2);
+    const unsigned long long bb = static_cast<unsigned long long>(__double_as_longlong(v));
+    if (bb - 1ull >= 0x7FEFFFFFFFFFFFFFull) return false;
+    lnb = df_add_s(lnb, df_from_double(log_table_split(v, logtab, e)));
+    lexp += e + 1;
+  }
+  if constexpr (GRAD)
+    mix_adjoint<float>(1.0f + Pm.hi, Q.hi, R.hi, S.hi, Zr.hi, Zi.hi, Ar.hi, Ai.hi, Br.hi, Bi.hi, bc.gammaf * th, tAr,
+                       tAi, tBr, tBi, gx, gy);
   return true;
 }
 
@@ -430,7 +560,7 @@ constexpr float kRecomputeCond = 16.0f;
 // |sinh w| <= sinh|w|, |w| <= |a| + |b|) and Z formed in fp32.
 template <int U>
 __device__ __forceinline__ bool ill_conditioned(const BlockConst<float>& bc, const float (&sc)[U], float Ar, float Ai,
-                                                float Br, float Bi, double t_e) {
+                                                float Br, float Bi, float t_e) {
   float SA = 0.f, SB = 0.f;
 #pragma unroll
   for (int j = 0; j < U; ++j) {
@@ -438,7 +568,7 @@ __device__ __forceinline__ bool ill_conditioned(const BlockConst<float>& bc, con
     SA = fmaf(fabsf(C.x) + fabsf(C.y), sc[j], SA);
     SB = fmaf(fabsf(C.z) + fabsf(C.w), sc[j], SB);
   }
-  const float tg = bc.gammaf * float(t_e);
+  const float tg = bc.gammaf * t_e;
   const float a = 0.5f * bc.yf * tg, b = 0.5f * bc.xf * tg;
   float cha, sha, cb, sb, chw, shw, c0, s0;
   mixing_trig_f32(a, b, cha, sha, cb, sb);
@@ -457,7 +587,7 @@ __device__ __forceinline__ bool ill_conditioned(const BlockConst<float>& bc, con
 // its registers must not add to the main loop's.
 template <class S>
 __device__ __noinline__ void df_amplitudes(const float* __restrict__ stage, const float* __restrict__ lo, int e,
-                                           const BlockConst<float>& bc, double* out) {
+                                           const BlockConst<float>& bc, DF* out) {
   constexpr int TE = kTileEvents;
   constexpr int NB = S::NB, NO = S::NO, U = S::U, NS = S::NS, NX = S::NX;
   constexpr int X0 = 2 * NS, K0 = 2 * NS + NX;
@@ -506,10 +636,10 @@ __device__ __noinline__ void df_amplitudes(const float* __restrict__ stage, cons
     Br = df_add(Br, df_sub(df_mul(cbr, sr), df_mul(cbi, si)));
     Bi = df_add(Bi, df_add(df_mul(cbr, si), df_mul(cbi, sr)));
   }
-  out[0] = df_to_double(Ar);
-  out[1] = df_to_double(Ai);
-  out[2] = df_to_double(Br);
-  out[3] = df_to_double(Bi);
+  out[0] = Ar;
+  out[1] = Ai;
+  out[2] = Br;
+  out[3] = Bi;
 }
 
 }  // namespace tdmix

@@ -215,6 +215,11 @@ __device__ inline void derive_compute(const ModelConst& km, CtaConst& cc, BlockC
     bc.xf = float(x);
     bc.yf = float(y);
     bc.gammaf = float(cc.gamma);
+    const DF hx2 = df_from_double(bc.hx), hy2 = df_from_double(bc.hy);
+    bc.hxh = hx2.hi;
+    bc.hxl = hx2.lo;
+    bc.hyh = hy2.hi;
+    bc.hyl = hy2.lo;
     // decay-time limits of the mixing-series tiers: |x|, |y| Gamma t / 2 <= 0.02, 0.1
     const double mg = fmax(fabs(x), fabs(y)) * cc.gamma;
     const double ig = mg > 0 ? rcp<double>(mg) : INFINITY;
@@ -528,6 +533,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   __shared__ double colsum[LY::W];
   __shared__ unsigned s_last, s_timeout;
   __shared__ double2 logtab[kLogTable];
+  __shared__ float4 logtab_f[P::kF32 ? kLogTable : 1];  // the same entries as double-float pairs
   // tensor-core normalisation matrix: MMA completion, TMEM base, column
   // exponents of the last three tiles (written, read, being reset)
   __shared__ __align__(8) uint64_t mma_bar;
@@ -602,7 +608,14 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
   }
   if (!FULL)  // stored MC totals of the fixed lineshapes
     for (int v = tid; v < WMC; v += kTile) colsum[v] = a.gram_store[v];
-  for (int j = tid; j < kLogTable; j += kTile) logtab[j] = static_cast<const double2*>(a.logtab)[j];
+  for (int j = tid; j < kLogTable; j += kTile) {
+    const double2 v = static_cast<const double2*>(a.logtab)[j];
+    logtab[j] = v;
+    if constexpr (P::kF32) {
+      const DF r = df_from_double(v.x), l = df_from_double(v.y);
+      logtab_f[j] = make_float4(r.hi, r.lo, l.hi, l.lo);
+    }
+  }
   // the parameter loads go out before the other tile copies flood the memory system
   derive_load<T, U>(a.params, a.hp, a.km, cc, bc);
   if constexpr (TCG) tc_fence_before_sync();
@@ -876,7 +889,8 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
     // completion counter are written only after that evaluation completed.
     grid_dependency_wait();
     {
-      double lnb = 0.0;  // sum ln B = lnb + lexp ln 2
+      double lnb = 0.0;     // sum ln B = lnb + lexp ln 2 (fp64 path)
+      DF lnbf{0.0f, 0.0f};  // the same as a double-float pair (fp32 path)
       int bad = 0, lexp = 0, n_rec = 0;
       T gx = 0, gy = 0, gAr[U], gAi[U], gBr[U], gBi[U], s1[NR > 0 ? NR : 1], s2[NR > 0 ? NR : 1];
 #pragma unroll
@@ -894,7 +908,9 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
         if (i < dd.n) {
           const unsigned char* stage = smem_raw + st * STB;
           const T* sbase = reinterpret_cast<const T*>(stage);
-          const double t_e = reinterpret_cast<const double*>(stage + NPL * TE * ES)[tid];
+          // decay time: a double (fp64 path) or a double-float pair (fp32 path)
+          const double t_e = P::kF32 ? 0.0 : reinterpret_cast<const double*>(stage + NPL * TE * ES)[tid];
+          const float2 t_f = P::kF32 ? reinterpret_cast<const float2*>(stage + NPL * TE * ES)[tid] : float2{0.f, 0.f};
           const SmemSrc<P, S, TE> src{sbase, tid, false};
           EventCore<P, S> ev;
           constexpr bool RECOMPUTE = RATES && FULL && P::kF32;
@@ -917,16 +933,23 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
           }
           T Ar_, Ai_, Br_, Bi_;
           ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
-          double Ad[4] = {double(Ar_), double(Ai_), double(Br_), double(Bi_)};
-          if constexpr (RECOMPUTE) {
-            if (ill_conditioned<U>(bc, sc, Ar_, Ai_, Br_, Bi_, t_e)) {
-              df_amplitudes<S>(sbase, dd.lo + tile * int64_t(S::NX + U * S::NO) * TE, tid, bc, Ad);
-              n_rec += 1;
-            }
-          }
           T tAr, tAi, tBr, tBi;
-          if (mix_event<P, GRAD>(bc, logtab, Ad[0], Ad[1], Ad[2], Ad[3], Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp,
-                                 a.rates ? a.rates + i : nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
+          bool ok_ev;
+          if constexpr (P::kF32) {
+            DF Ad[4] = {DF{Ar_, 0.0f}, DF{Ai_, 0.0f}, DF{Br_, 0.0f}, DF{Bi_, 0.0f}};
+            if constexpr (RECOMPUTE) {
+              if (ill_conditioned<U>(bc, sc, Ar_, Ai_, Br_, Bi_, t_f.x)) {
+                df_amplitudes<S>(sbase, dd.lo + tile * int64_t(S::NX + U * S::NO) * TE, tid, bc, Ad);
+                n_rec += 1;
+              }
+            }
+            ok_ev = mix_event_df<GRAD>(bc, logtab, logtab_f, Ad[0], Ad[1], Ad[2], Ad[3], t_f.x, t_f.y, lnbf, lexp,
+                                       a.rates ? a.rates + i : nullptr, tAr, tAi, tBr, tBi, gx, gy);
+          } else {
+            ok_ev = mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp,
+                                       a.rates ? a.rates + i : nullptr, tAr, tAi, tBr, tBi, gx, gy);
+          }
+          if (ok_ev) {
             if constexpr (GRAD) {
 #pragma unroll
               for (int j = 0; j < U; ++j) {
@@ -944,7 +967,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
       // block sums of the data accumulators -> rowp[WMC ..]
       {
         __shared__ int red_bad[kWarps], red_rec[kWarps];
-        const double v0 = warp_sum(fma(double(lexp), kLn2, lnb));
+        const double v0 = warp_sum(fma(double(lexp), kLn2, P::kF32 ? df_to_double(lnbf) : lnb));
         const int v1 = warp_sum(bad);
         const int v2 = warp_sum(n_rec);
         if (lane == 0) {

@@ -17,8 +17,9 @@ namespace tdmix {
 // factors X(s) = q^(2L+1) F_L(q r)^2 / sqrt(s) and the spin x barrier factor
 // K_{j,o} of every component ordering.  None depends on fit parameters.
 // Written tile-major (the layout of SampleDev): event i is slot i % 256 of
-// tile i / 256; after the planes of a tile come its decay times (data) or
-// weights (weighted MC); the decay times also go to the component-cache tile.
+// tile i / 256; after the planes of a tile come its decay times (data: a
+// double each in fp64 tiles, a double-float pair in fp32 tiles) or weights
+// (weighted MC); the decay times also go to the component-cache tile.
 // ---------------------------------------------------------------------------
 template <bool F32>
 __global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, const DevModel* __restrict__ dm,
@@ -76,9 +77,17 @@ __global__ void __launch_bounds__(256) k_precompute(Momenta mom, int64_t n, cons
   }
   unsigned char* extra = planes + tile * tile_bytes + int64_t(npl) * TE * sizeof(T);
   if (t) {
-    reinterpret_cast<double*>(extra)[e] = t[i];
-    if (cache)
-      reinterpret_cast<double*>(cache + tile * cache_tile_bytes + int64_t(2 * dm->U) * TE * sizeof(T))[e] = t[i];
+    // the decay time: a double (fp64 tiles) or a double-float pair (fp32 tiles)
+    unsigned char* tc = cache ? cache + tile * cache_tile_bytes + int64_t(2 * dm->U) * TE * sizeof(T) : nullptr;
+    if constexpr (F32) {
+      const float hi = float(t[i]);
+      const float2 v = make_float2(hi, float(t[i] - double(hi)));
+      reinterpret_cast<float2*>(extra)[e] = v;
+      if (tc) reinterpret_cast<float2*>(tc)[e] = v;
+    } else {
+      reinterpret_cast<double*>(extra)[e] = t[i];
+      if (tc) reinterpret_cast<double*>(tc)[e] = t[i];
+    }
   } else if (w) {
     reinterpret_cast<T*>(extra)[e] = T(w[i]);
   }

@@ -78,13 +78,21 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
   __shared__ float2 rowp[WD];
   __shared__ double colsum[WMC + WD];
   __shared__ double2 logtab[kLogTable];
+  __shared__ float4 logtab_f[P::kF32 ? kLogTable : 1];  // the same entries as double-float pairs
   __shared__ long long s_entry;
   __shared__ int s_chunk, s_slot;
   __shared__ unsigned s_last;
   __shared__ ServeSlot s_req;  // the request's fields (one read of mapped memory)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned char* stage[2] = {smem_raw, smem_raw + LY::stage_bytes};
-  for (int j = tid; j < kLogTable; j += blockDim.x) logtab[j] = static_cast<const double2*>(a.logtab)[j];
+  for (int j = tid; j < kLogTable; j += blockDim.x) {
+    const double2 v = static_cast<const double2*>(a.logtab)[j];
+    logtab[j] = v;
+    if constexpr (P::kF32) {
+      const DF r = df_from_double(v.x), l = df_from_double(v.y);
+      logtab_f[j] = make_float4(r.hi, r.lo, l.hi, l.lo);
+    }
+  }
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -174,7 +182,8 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
     derive_compute<T, U, NR>(a.km, cc, bc);
     __syncthreads();
 
-    double lnb = 0.0;  // sum ln B = lnb + lexp ln 2
+    double lnb = 0.0;     // sum ln B = lnb + lexp ln 2 (fp64 path)
+    DF lnbf{0.0f, 0.0f};  // the same as a double-float pair (fp32 path)
     int bad = 0, lexp = 0;
     bool failed = false;
     int failed_at = 0;
@@ -192,7 +201,10 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
       const int64_t i = int64_t(t0 + j) * TE + tid;
       if (i < n_ev) {
         const T* sbase = reinterpret_cast<const T*>(stage[st]);
-        const double t_e = reinterpret_cast<const double*>(stage[st] + 2 * U * TE * ES)[tid];
+        // decay time: a double (fp64 path) or a double-float pair (fp32 path)
+        const unsigned char* tplane = stage[st] + 2 * U * TE * ES;
+        const double t_e = P::kF32 ? 0.0 : reinterpret_cast<const double*>(tplane)[tid];
+        const float2 t_f = P::kF32 ? reinterpret_cast<const float2*>(tplane)[tid] : float2{0.f, 0.f};
         EventCore<P, S> ev;
 #pragma unroll
         for (int k = 0; k < U; ++k) {
@@ -202,8 +214,14 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
         T Ar_, Ai_, Br_, Bi_;
         ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
         T tAr, tAi, tBr, tBi;
-        if (mix_event<P, GRAD>(bc, logtab, double(Ar_), double(Ai_), double(Br_), double(Bi_), Ar_, Ai_, Br_, Bi_,
-                               t_e, lnb, lexp, nullptr, tAr, tAi, tBr, tBi, gx, gy)) {
+        bool ok_ev;
+        if constexpr (P::kF32)
+          ok_ev = mix_event_df<GRAD>(bc, logtab, logtab_f, DF{Ar_, 0.0f}, DF{Ai_, 0.0f}, DF{Br_, 0.0f},
+                                     DF{Bi_, 0.0f}, t_f.x, t_f.y, lnbf, lexp, nullptr, tAr, tAi, tBr, tBi, gx, gy);
+        else
+          ok_ev = mix_event<P, GRAD>(bc, logtab, Ar_, Ai_, Br_, Bi_, Ar_, Ai_, Br_, Bi_, t_e, lnb, lexp, nullptr, tAr,
+                                     tAi, tBr, tBi, gx, gy);
+        if (ok_ev) {
           if constexpr (GRAD) {
 #pragma unroll
             for (int k = 0; k < U; ++k) {
@@ -232,7 +250,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
     }
     // chunk partial -> its row (double-float; see block_sum_df)
     {
-      const double v0 = warp_sum(fma(double(lexp), kLn2, lnb));
+      const double v0 = warp_sum(fma(double(lexp), kLn2, P::kF32 ? df_to_double(lnbf) : lnb));
       const int v1 = warp_sum(bad);
       if (lane == 0) {
         red_lnb[warp] = v0;

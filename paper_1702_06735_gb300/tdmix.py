@@ -93,7 +93,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 
 
 MATH_CODES = {"log_table": 0, "log_cuda": 1, "rcp_f64": 2, "div_f64": 3, "rcp_f32": 4, "div_f32": 5,
-              "df_rcp": 6, "mix_tier0": 7, "mix_tier1": 8, "mix_tier2": 9}
+              "df_rcp": 6, "mix_tier0": 7, "mix_tier1": 8, "mix_tier2": 9, "log_df": 10, "eqmix_df": 11,
+              "eqmix_f64": 12}
 
 
 def test_philox(counter, key):
@@ -111,15 +112,18 @@ def test_philox(counter, key):
 def test_math(which: str, v) -> np.ndarray:
     """Evaluates one of the kernels' math routines (or the CUDA function it
     replaces) on the device: tdmix_test_math.  Returns n values, or (n, 4)
-    (cosh, sinh, cos, sin) for the mixing-series codes."""
+    (cosh, sinh, cos, sin) for the mixing-series codes; the Eq. (mix) codes
+    ("eqmix_df", "eqmix_f64") take (n, 8) records {Ar, Ai, Br, Bi, t, x, y,
+    Gamma} and return (n, 4) {ln B, e^{-Gamma t} B, ok, 0}."""
     lib = load_library()
     a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
-    per = 4 if which.startswith("mix") else 1
-    out = np.empty(per * len(a))
-    rc = lib.tdmix_test_math(MATH_CODES[which], len(a), a.ctypes.data, out.ctypes.data)
+    n = a.shape[0]
+    per = 4 if which.startswith("mix") or which.startswith("eqmix") else 1
+    out = np.empty(per * n)
+    rc = lib.tdmix_test_math(MATH_CODES[which], n, a.ctypes.data, out.ctypes.data)
     if rc != 0:
         raise TDMixError(rc, "tdmix_test_math")
-    return out.reshape(len(a), 4) if per == 4 else out
+    return out.reshape(n, 4) if per == 4 else out
 
 
 class Events(ctypes.Structure):
