@@ -61,15 +61,25 @@ typedef enum {
   TDMIX_ERR_NONFINITE = -5, /* non-finite parameter, or a rate <= 0 / not finite */
   TDMIX_ERR_DOMAIN = -6,    /* |y| >= 1, mass or width <= 0, pole below threshold */
   TDMIX_ERR_TIMEOUT = -7,   /* a bounded wait gave up */
-  TDMIX_ERR_UNSUPPORTED = -8 /* model structure not compiled into the library */
+  TDMIX_ERR_UNSUPPORTED = -8 /* operation not available for this context (see tdmix_create) */
 } tdmix_status;
 
 typedef enum {
   TDMIX_FP64 = 0, /* every per-event quantity in float64 */
-  TDMIX_FP32 = 1  /* lineshapes, spin factors and coherent sums in float32;
+  TDMIX_FP32 = 1, /* lineshapes, spin factors and coherent sums in float32;
                      mixing terms, log-likelihood sum and normalisation
                      accumulation in float64 */
+  TDMIX_GENERIC = 0x100 /* flag, OR-ed into the precision: evaluate with the
+                     runtime-table kernels even where the model's structure
+                     has a compiled specialisation (comparisons, tests) */
 } tdmix_precision;
+
+/* Which kernels a context evaluates with (tdmix_kernel_path). */
+typedef enum {
+  TDMIX_PATH_FP64 = 0,   /* structure-specialised kernels, float64 */
+  TDMIX_PATH_FP32 = 1,   /* structure-specialised kernels, precision path */
+  TDMIX_PATH_GENERIC = 2 /* runtime-table kernels, float64 */
+} tdmix_kernel_path_kind;
 
 /* One event sample in structure-of-arrays form.
  *   n          number of events (>= 1)
@@ -91,9 +101,24 @@ typedef struct {
  * for the schema) on the current CUDA device.  Recurring building blocks are
  * shared (Sec. 3: recurring form factors, spin factors and lineshapes are
  * linked to one instance).  *out receives the context; TDMIX_ERR_ARG for an
- * invalid model, TDMIX_ERR_UNSUPPORTED if its structure was not compiled
- * into the library. */
+ * invalid model or precision.
+ * The kernels are specialised at build time on the structures of the
+ * shipped model files (which lineshapes enter which term of which
+ * component).  A model of any other structure - the user composes chains,
+ * amplitudes and the time-dependent model (Sec. 3) - is evaluated by the
+ * runtime-table kernels instead: the same likelihood and gradient, in
+ * float64 whatever precision was asked for (so within the tolerances of
+ * both paths), several times slower, with every evaluation a full one (no
+ * component cache) and without the serving loop (tdmix_server_create
+ * returns TDMIX_ERR_UNSUPPORTED) or the device generator (tdmix_generate
+ * returns TDMIX_ERR_UNSUPPORTED).  tdmix_kernel_path tells which kernels a
+ * context uses; precision | TDMIX_GENERIC selects the runtime-table kernels
+ * for any model. */
 int tdmix_create(const char* model_json, int precision, tdmix_ctx** out);
+
+/* The kernels the context evaluates with (tdmix_kernel_path_kind), or a
+ * negative status. */
+int tdmix_kernel_path(const tdmix_ctx* ctx);
 
 /* Uses the given cudaStream_t (NULL: the legacy default stream) for all
  * later work of the context. */

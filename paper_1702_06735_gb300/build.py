@@ -62,6 +62,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         ("eval_inst.cu", "eval_f32.o", ["-DTDMIX_PREC_F32=1"]),
         ("capi.cu", "capi.o", []),
         ("noalloc.cu", "noalloc.o", []),
+        ("generic.cu", "generic.o", []),
         ("selftest.cu", "selftest.o", []),
         ("serve.cu", "serve.o", []),
         ("model.cpp", "model.o", []),

@@ -42,6 +42,8 @@ struct tdmix_ctx {
   CompiledModel model;
   bool f32 = false;
   const ShapeOps* ops = nullptr;
+  bool generic = false;   // runtime-table evaluation (no compiled specialisation of the structure)
+  ShapeOps generic_ops{};  // ops of the generic path (ops points here when generic)
   cudaStream_t stream = nullptr;
   int device = 0, num_sms = 0;
   DevModel* d_model = nullptr;  // structure tables of the kinematic precompute
@@ -144,6 +146,13 @@ DevModel make_dev_model(const CompiledModel& m) {
   for (size_t t = 0; t < m.terms.size(); ++t) {
     d.term_spin[t] = m.terms[t].spin;
     for (int k = 0; k < 4; ++k) d.term_parts[t][k] = m.terms[t].parts[k];
+    d.term_bw[t][0] = m.terms[t].b[0];
+    d.term_bw[t][1] = m.terms[t].b[1];
+  }
+  for (size_t b = 0; b < m.bws.size(); ++b) {
+    d.bw_res[b] = m.bws[b].res;
+    d.bw_splane[b] = m.bws[b].splane;
+    d.bw_xplane[b] = m.bws[b].xplane;
   }
   for (int s = 0; s < m.NS(); ++s) d.splane_mask[s] = m.splane_mask[s];
   for (int x = 0; x < m.NX(); ++x) {
@@ -175,6 +184,30 @@ ModelConst make_model_const(const CompiledModel& m, const std::vector<int>& floa
   }
   for (int q = 0; q < m.n_params(); ++q) k.floating[q] = floating[q] ? 1 : 0;
   return k;
+}
+
+cudaError_t generic_serve(int, cudaStream_t, const ServeLoopArgs&) { return cudaErrorNotSupported; }
+
+// Layout of the generic path: fp64 planes of the kinematic precompute.
+ShapeOps make_generic_ops(const CompiledModel& m) {
+  ShapeOps o{};
+  const int U = m.U, NR = m.NR();
+  const int npl = m.NS() + m.NX() + U * m.NO;
+  const int64_t plane_bytes = int64_t(npl) * kTileEvents * sizeof(double), extra = kTileEvents * sizeof(double);
+  o.signature = "generic";
+  o.U = U;
+  o.NR = NR;
+  o.mc_width = 1 + U * (U + 1) / 2 + U * (U - 1) / 2 + 2 * NR;
+  o.data_width = 5 + 4 * U + 2 * NR;
+  o.n_planes = npl;
+  o.data_tile_bytes = plane_bytes + extra;
+  o.mc_tile_bytes = plane_bytes;
+  o.mc_tile_bytes_weighted = plane_bytes + extra;
+  o.cache_tile_bytes = int64_t(2 * U) * kTileEvents * sizeof(double) + extra;
+  o.eval = &generic_eval;
+  o.serve = &generic_serve;
+  o.serve_row_stride = 0;
+  return o;
 }
 
 }  // namespace
@@ -383,8 +416,10 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   bool res_floating = false;
   for (int k = 2 * nc; k < 2 * nc + 2 * m.NR(); ++k) res_floating |= ctx->floating[k] != 0;
   // per-event rates always come from a full evaluation (the recomputation
-  // of ill-conditioned events of the fp32 path runs there)
-  bool full = data_only || rates != nullptr || !host_params || !ctx->cache_valid || (want_grad && res_floating);
+  // of ill-conditioned events of the fp32 path runs there); the generic path
+  // keeps no component cache
+  bool full = data_only || rates != nullptr || !host_params || !ctx->cache_valid || (want_grad && res_floating) ||
+              ctx->generic;
   if (host_params && !full) {
     for (int k = 0; k < 2 * m.NR(); ++k)
       if (params[2 * nc + k] != ctx->last_res[k]) full = true;
@@ -413,6 +448,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.logtab = ctx->d_logtab;
   a.withhold_first_copy = ctx->withhold_first_copy ? 1 : 0;
   a.gram_pref = ctx->gram_pref;
+  a.dm = ctx->d_model;
   a.sum_t = ctx->sum_t;
   a.inv_sum_w = ctx->inv_sum_w;
   a.trace = ctx->d_trace;
@@ -483,6 +519,7 @@ const ShapeOps* ops_of(tdmix_ctx* ctx) { return ctx->ops; }
 const ModelConst& model_const_of(tdmix_ctx* ctx) { return ctx->km; }
 const void* log_table_of(tdmix_ctx* ctx) { return ctx->d_logtab; }
 bool is_f32(tdmix_ctx* ctx) { return ctx->f32; }
+bool is_generic(tdmix_ctx* ctx) { return ctx->generic; }
 double inv_sum_w_of(tdmix_ctx* ctx) { return ctx->inv_sum_w; }
 const double* gram_store_of(tdmix_ctx* ctx) { return ctx->d_gram; }
 std::string& error_of(tdmix_ctx* ctx) { return ctx->err; }
@@ -531,6 +568,8 @@ extern "C" {
 int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   if (!out || !model_json) return TDMIX_ERR_ARG;
   *out = nullptr;
+  const bool force_generic = (precision & TDMIX_GENERIC) != 0;
+  precision &= ~TDMIX_GENERIC;
   if (precision != TDMIX_FP64 && precision != TDMIX_FP32) return TDMIX_ERR_ARG;
   tdmix_ctx* ctx = new (std::nothrow) tdmix_ctx;
   if (!ctx) return TDMIX_ERR_NOMEM;
@@ -543,12 +582,15 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
     return TDMIX_ERR_ARG;
   }
   ctx->f32 = precision == TDMIX_FP32;
-  ctx->ops = find_shape_ops(ctx->model.signature(), ctx->f32);
+  ctx->ops = force_generic ? nullptr : find_shape_ops(ctx->model.signature(), ctx->f32);
   *out = ctx;
-  if (!ctx->ops)
-    return fail(ctx, TDMIX_ERR_UNSUPPORTED,
-                "model structure not compiled into the library (add the model file and rebuild): " +
-                    ctx->model.signature());
+  if (!ctx->ops) {
+    // no specialisation of this structure: the runtime-table kernels, in fp64
+    ctx->generic = true;
+    ctx->f32 = false;
+    ctx->generic_ops = make_generic_ops(ctx->model);
+    ctx->ops = &ctx->generic_ops;
+  }
   TDMIX_CK(cudaGetDevice(&ctx->device));
   TDMIX_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
   const int np = ctx->model.n_params();
@@ -590,6 +632,11 @@ int tdmix_set_stream(tdmix_ctx* ctx, void* cuda_stream) {
 }
 
 int tdmix_num_params(const tdmix_ctx* ctx) { return ctx ? ctx->model.n_params() : TDMIX_ERR_ARG; }
+
+int tdmix_kernel_path(const tdmix_ctx* ctx) {
+  if (!ctx || !ctx->ops) return TDMIX_ERR_ARG;
+  return ctx->generic ? TDMIX_PATH_GENERIC : (ctx->f32 ? TDMIX_PATH_FP32 : TDMIX_PATH_FP64);
+}
 
 int tdmix_num_components(const tdmix_ctx* ctx) { return ctx ? ctx->model.U : TDMIX_ERR_ARG; }
 
@@ -903,6 +950,8 @@ int tdmix_set_gram(tdmix_ctx* ctx, int mode) {
   if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
   if (mode != TDMIX_GRAM_AUTO && mode != TDMIX_GRAM_REGISTERS && mode != TDMIX_GRAM_TENSOR)
     return fail(ctx, TDMIX_ERR_ARG, "unknown normalisation-matrix mode");
+  if (ctx->generic && mode != TDMIX_GRAM_AUTO)
+    return fail(ctx, TDMIX_ERR_UNSUPPORTED, "the generic evaluation has one normalisation-matrix mode");
   if (mode == TDMIX_GRAM_TENSOR && !ctx->f32)
     return fail(ctx, TDMIX_ERR_UNSUPPORTED, "the tensor-core normalisation matrix runs on the fp32 path");
   if (mode == TDMIX_GRAM_REGISTERS && ctx->model.U > 8)

@@ -21,6 +21,11 @@ struct DevModel {
   int xplane_s[kMaxXPlanes];
   int xplane_L[kMaxXPlanes];
   double xplane_ma[kMaxXPlanes], xplane_mb[kMaxXPlanes];
+  // lineshape structure, read by the runtime-table (generic) evaluation:
+  // Breit-Wigner instances of each term (-1: none) and, per instance, its
+  // resonance, invariant plane and width plane (-1: constant width)
+  int term_bw[kMaxTerms][2];
+  int bw_res[kMaxBW], bw_splane[kMaxBW], bw_xplane[kMaxBW];
 };
 
 // Model constants the likelihood kernels read, passed by value in the
@@ -87,6 +92,7 @@ struct EvalArgs {
   int withhold_first_copy;    // test hook: block 0 does not issue its first tile copy, so its
                               // bounded wait for that tile runs out (TDMIX_ERR_TIMEOUT)
   int gram_pref;              // how to accumulate the MC normalisation matrix (TDMIX_GRAM_*)
+  const DevModel* dm;         // structure tables (read by the generic evaluation only)
 };
 
 // Phases stamped by the evaluation kernel when tracing is on: start,

@@ -43,6 +43,10 @@ struct ShapeOps {
   int serve_row_stride;  // float2 entries per chunk-partial row
 };
 
+// Launcher of the runtime-table evaluation (generic.cu) for model
+// structures without a compiled specialisation; fits ShapeOps::eval.
+cudaError_t generic_eval(bool full, bool grad, int grid, bool pdl, cudaStream_t st, const EvalArgs& a);
+
 // Table of the kernels' logarithm ({1/F, ln F} pairs, F = 1 + j/128).
 std::vector<double> make_log_table();
 

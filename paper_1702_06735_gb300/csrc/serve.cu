@@ -46,6 +46,7 @@ const void* log_table_of(tdmix_ctx* ctx);
 double inv_sum_w_of(tdmix_ctx* ctx);
 const double* gram_store_of(tdmix_ctx* ctx);
 std::string& error_of(tdmix_ctx* ctx);
+bool is_generic(tdmix_ctx* ctx);
 int take_component_cache(tdmix_ctx* ctx, const tdmix_events* ev, const double* params, void** cache,
                          int64_t* tile_bytes, double* sum_t);
 int compute_mc_totals(tdmix_ctx* ctx, const double* params, const tdmix_events* one_event);
@@ -511,6 +512,10 @@ int tdmix_server_create(const char* model_json, int precision, size_t hbm_budget
   if (cudaGetDevice(&s->device) != cudaSuccess) return sfail(s, TDMIX_ERR_CUDA, "no CUDA device");
   int rc = tdmix_create(model_json, precision, &s->ctx);
   if (rc) return sfail(s, rc, s->ctx ? tdmix_last_error(s->ctx) : "model");
+  if (internal::is_generic(s->ctx))
+    return sfail(s, TDMIX_ERR_UNSUPPORTED,
+                 "serving needs a model structure compiled into the library (the generic evaluation keeps no "
+                 "component cache)");
   cudaStream_t st;
   SV_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   tdmix_set_stream(s->ctx, st);

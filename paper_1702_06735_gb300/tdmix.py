@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "libtdmix.so")
 MODEL_DIR = os.path.join(HERE, "amplitude_models")
 
 FP64, FP32 = 0, 1
+GENERIC = 0x100      # flag: the runtime-table kernels whatever the structure
+KERNEL_PATHS = {0: "fp64", 1: "fp32", 2: "generic"}
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_STATE", -5: "ERR_NONFINITE",
           -6: "ERR_DOMAIN", -7: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
 
@@ -29,6 +31,7 @@ _SIGNATURES = {
     "tdmix_create": (_c_i, [ctypes.c_char_p, _c_i, ctypes.POINTER(_c_p)]),
     "tdmix_set_stream": (_c_i, [_c_p, _c_p]),
     "tdmix_num_params": (_c_i, [_c_p]),
+    "tdmix_kernel_path": (_c_i, [_c_p]),
     "tdmix_num_components": (_c_i, [_c_p]),
     "tdmix_chain_component": (_c_i, [_c_p, _c_i]),
     "tdmix_default_params": (_c_i, [_c_p, _c_p]),
@@ -187,10 +190,10 @@ def _planes(p4, t=None, w=None):
 class TDMix:
     """One likelihood context (tdmix_ctx) on the current CUDA device."""
 
-    def __init__(self, model, precision: str = "fp64", stream=None):
+    def __init__(self, model, precision: str = "fp64", stream=None, generic: bool = False):
         self._lib = load_library()
         self._ctx = ctypes.c_void_p()
-        prec = {"fp64": FP64, "fp32": FP32}[precision]
+        prec = {"fp64": FP64, "fp32": FP32}[precision] | (GENERIC if generic else 0)
         self.precision = precision
         rc = self._lib.tdmix_create(model_json(model).encode(), prec, ctypes.byref(self._ctx))
         if rc != 0:
@@ -203,6 +206,10 @@ class TDMix:
             self.set_stream(stream)
         self.n_params = self._lib.tdmix_num_params(self._ctx)
         self.n_components = self._lib.tdmix_num_components(self._ctx)
+        # "fp64", "fp32" (structure-specialised kernels) or "generic"
+        # (runtime-table kernels, float64: a structure without a compiled
+        # specialisation, or generic=True)
+        self.kernel_path = KERNEL_PATHS[self._lib.tdmix_kernel_path(self._ctx)]
 
     def _check(self, rc):
         if rc != 0:

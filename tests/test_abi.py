@@ -70,19 +70,25 @@ def test_null_arguments(lib):
     assert lib.tdmix_last_error(None) == b"null context"
 
 
-def test_model_beyond_the_compiled_specialisations_is_refused(lib):
+def test_model_beyond_the_compiled_specialisations_passes_the_model_checks(lib):
     """A structure none of the shipped model files has (the 2-chain model
-    plus a D-wave K*0 rho0 chain) is not compiled into the library: creation
-    reports TDMIX_ERR_UNSUPPORTED (before any device call) with a message."""
+    plus a D-wave K*0 rho0 chain) is a valid model: creation gets past the
+    model compiler and the structure lookup (the runtime-table kernels take
+    it) and, without a GPU, stops only at the first device call."""
     import copy
+    import ctypes
     import json
     from conftest import model_path
-    from paper_1702_06735_gb300.tdmix import TDMix, TDMixError
     d = json.load(open(model_path("d0_k3pi_2chain")))
     extra = copy.deepcopy(d["chains"][0])
     extra.update(name="CF K*0 rho0 D-wave", spin="VV_D", coef=[0.3, 0.1], float=True)
     d["chains"].append(extra)
-    with pytest.raises(TDMixError) as e:
-        TDMix(d, "fp32")
-    assert e.value.code == -8
-    assert "not compiled" in str(e.value)
+    ctx = ctypes.c_void_p()
+    rc = lib.tdmix_create(json.dumps(d).encode(), 1, ctypes.byref(ctx))
+    try:
+        if rc == 0:   # a GPU is present
+            assert lib.tdmix_kernel_path(ctx) == 2
+        else:
+            assert rc == -3, lib.tdmix_last_error(ctx)
+    finally:
+        lib.tdmix_destroy(ctx)
