@@ -61,6 +61,8 @@ struct tdmix_ctx {
   double* d_result_map = nullptr;  // device address of h_result
   void* d_part = nullptr;         // block partials of the evaluation kernel (float2 [num_sms][width])
   unsigned* d_counter = nullptr;  // blocks finished (returned to 0 by the kernel)
+  void* d_derived = nullptr;      // per-evaluation constants of a batch (k_derive records)
+  int64_t derived_cap = 0;        // records d_derived holds
   Sample data, mc;
   double sum_t = 0;
   double inv_sum_w = 1.0;  // 1 / sum of MC weights
@@ -207,6 +209,8 @@ ShapeOps make_generic_ops(const CompiledModel& m) {
   o.eval = &generic_eval;
   o.serve = &generic_serve;
   o.serve_row_stride = 0;
+  o.derive = nullptr;
+  o.derived_bytes = 0;
   return o;
 }
 
@@ -408,7 +412,7 @@ int load_sample(tdmix_ctx* ctx, const tdmix_events* ev, bool is_data, Sample& s)
 // prof: record profiling events around this launch.
 int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool want_grad, double* rates,
                  double* result, double* out_nll = nullptr, double* out_grad = nullptr, bool data_only = false,
-                 bool pdl = false, int grid_cap = 0, bool prof = true) {
+                 bool pdl = false, int grid_cap = 0, bool prof = true, const void* derived = nullptr) {
   const CompiledModel& m = ctx->model;
   const int np = m.n_params(), nc = int(m.chains.size());
   cudaStream_t st = ctx->stream;
@@ -449,6 +453,7 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   a.withhold_first_copy = ctx->withhold_first_copy ? 1 : 0;
   a.gram_pref = ctx->gram_pref;
   a.dm = ctx->d_model;
+  a.derived = derived;
   a.sum_t = ctx->sum_t;
   a.inv_sum_w = ctx->inv_sum_w;
   a.trace = ctx->d_trace;
@@ -457,13 +462,15 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
     // data tiles q, q + grid, ... and MC tiles [range[q], range[q + 1]).
     const int64_t n_dt = ctx->data.dev.n_tiles, n_mt = ctx->mc.dev.n_tiles;
     if (ctx->ranges_key[0] != n_dt || ctx->ranges_key[1] != n_mt || ctx->ranges_key[2] != grid) {
-      const int64_t R = ctx->f32 ? kDataTileCostF32 : kDataTileCostF64;
-      const int64_t total = R * n_dt + n_mt, G = grid;
+      const int64_t Rd = ctx->f32 ? kDataTileCostF32 : kDataTileCostF64;
+      const int64_t Rm = ctx->f32 ? kMcTileCostF32 : kMcTileCostF64;
+      const int64_t total = Rd * n_dt + Rm * n_mt, G = grid;
       std::vector<int64_t> rg(G + 1, 0);
       int64_t run = 0, data_upto = 0;
       for (int64_t q = 0; q < G; ++q) {
         data_upto += n_dt > q ? (n_dt - 1 - q) / G + 1 : 0;  // data tiles of blocks <= q
-        int64_t e = (q + 1) * total / G - R * data_upto;
+        // MC tiles of blocks <= q: their share of the cost units, less their data tiles'
+        int64_t e = ((q + 1) * total / G - Rd * data_upto + Rm / 2) / Rm;
         e = e < 0 ? 0 : (e > n_mt ? n_mt : e);
         run = e > run ? e : run;
         rg[q + 1] = q == G - 1 ? n_mt : run;
@@ -627,6 +634,8 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
 
 int tdmix_set_stream(tdmix_ctx* ctx, void* cuda_stream) {
   if (!ctx) return TDMIX_ERR_ARG;
+  // work enqueued on the old stream completes before buffers are reused on the new one
+  if (ctx->ops && ctx->stream != static_cast<cudaStream_t>(cuda_stream)) TDMIX_CK(cudaStreamSynchronize(ctx->stream));
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   return TDMIX_OK;
 }
@@ -704,6 +713,7 @@ int tdmix_nll_batch(tdmix_ctx* ctx, const double* params, int64_t n_points, doub
   if (!ctx->ops) return fail(ctx, TDMIX_ERR_STATE, "context has no compiled model");
   if (!is_device_ptr(params) || !is_device_ptr(nll_out) || (grad_out && !is_device_ptr(grad_out)))
     return fail(ctx, TDMIX_ERR_ARG, "a batch takes device parameters and device outputs");
+  if (n_points > (int64_t(1) << 30)) return fail(ctx, TDMIX_ERR_ARG, "too many points in one batch");
   cudaGetLastError();
   const int np = ctx->model.n_params();
   // Consecutive evaluations overlap: each may start while the one before it
@@ -712,9 +722,24 @@ int tdmix_nll_batch(tdmix_ctx* ctx, const double* params, int64_t n_points, doub
   const int cap = n_points > 1 && ctx->num_sms > 1 ? ctx->num_sms - 1 : ctx->num_sms;
   int rc;
   if ((rc = prof_mark(ctx, TDMIX_PROF_EVAL, 0))) return rc;
+  // the constants of every point are derived once, by one launch, before the evaluations
+  const unsigned char* derived = nullptr;
+  if (ctx->ops->derive && n_points > 1) {
+    const int64_t rb = ctx->ops->derived_bytes;
+    if (ctx->derived_cap < n_points) {
+      if (ctx->d_derived) TDMIX_CK(cudaFreeAsync(ctx->d_derived, ctx->stream));
+      ctx->d_derived = nullptr;
+      ctx->derived_cap = 0;
+      TDMIX_CK(cudaMallocAsync(&ctx->d_derived, size_t(n_points * rb), ctx->stream));
+      ctx->derived_cap = n_points;
+    }
+    TDMIX_CK(ctx->ops->derive(int(n_points), params, np, ctx->km, ctx->d_derived, ctx->stream));
+    derived = static_cast<const unsigned char*>(ctx->d_derived);
+  }
   for (int64_t k = 0; k < n_points; ++k) {
     rc = enqueue_eval(ctx, params + k * np, false, grad_out != nullptr, nullptr, ctx->d_result, nll_out + k,
-                      grad_out ? grad_out + k * np : nullptr, false, k > 0, cap, false);
+                      grad_out ? grad_out + k * np : nullptr, false, k > 0, cap, false,
+                      derived ? derived + k * ctx->ops->derived_bytes : nullptr);
     if (rc) return rc;
   }
   return prof_mark(ctx, TDMIX_PROF_EVAL, 1, n_points);
@@ -1012,6 +1037,7 @@ void tdmix_destroy(tdmix_ctx* ctx) {
   if (ctx->ops) cudaStreamSynchronize(ctx->stream);
   free_sample(ctx->data, ctx->stream);
   free_sample(ctx->mc, ctx->stream);
+  if (ctx->d_derived) cudaFreeAsync(ctx->d_derived, ctx->stream);
   if (ctx->ops) cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->d_model);
   cudaFree(ctx->d_result);

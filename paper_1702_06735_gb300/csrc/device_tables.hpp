@@ -93,6 +93,8 @@ struct EvalArgs {
                               // bounded wait for that tile runs out (TDMIX_ERR_TIMEOUT)
   int gram_pref;              // how to accumulate the MC normalisation matrix (TDMIX_GRAM_*)
   const DevModel* dm;         // structure tables (read by the generic evaluation only)
+  const void* derived;        // per-evaluation constants derived for a batch (k_derive), or null:
+                              // every block derives them from the parameters
 };
 
 // Phases stamped by the evaluation kernel when tracing is on: start,
@@ -100,10 +102,13 @@ struct EvalArgs {
 // the last block: column totals formed, result written; end.
 constexpr int kTracePhases = 8;
 
-// Relative cost of one data tile in units of one MC tile (used to balance
-// the static assignment of tiles to blocks).
-constexpr int kDataTileCostF32 = 4;
-constexpr int kDataTileCostF64 = 1;
+// Relative cost of one data tile and one MC tile, in common units (used to
+// balance the static assignment of tiles to blocks).  fp32: a data tile
+// (double-float Eq. (mix), its adjoint and the component-cache write) takes
+// about 5/3 of an MC tile, measured per block with the trace stamps (2.2 us
+// against 1.34 us on GB300); fp64: about equal.
+constexpr int kDataTileCostF32 = 5, kMcTileCostF32 = 3;
+constexpr int kDataTileCostF64 = 1, kMcTileCostF64 = 1;
 
 // Result vector written by the evaluation kernel:
 // [nll, N, n_bad or status, sum ln B, data events recomputed in double-float, grad...]

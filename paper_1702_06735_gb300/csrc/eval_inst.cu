@@ -114,6 +114,10 @@ struct Ops {
     }
     return cudaErrorNotSupported;
   }
+  static cudaError_t derive(int K, const double* params, int np, const ModelConst& km, void* out, cudaStream_t st) {
+    k_derive<Prec, S><<<K, kTile, 0, st>>>(params, np, km, static_cast<DerivedConst<typename Prec::T>*>(out));
+    return cudaGetLastError();
+  }
   static cudaError_t serve(int grid, cudaStream_t st, const ServeLoopArgs& a) {
     if constexpr (kOk) {
       const int smem = ServeLayout<Prec, S>::smem_bytes();
@@ -166,7 +170,8 @@ const ShapeOps* TDMIX_FIND(const std::string& sig) {
                                LY_::NPL_FULL, LY_::data_tile_bytes(), LY_::mc_tile_bytes(false), \
                                LY_::mc_tile_bytes(true), LY_::cache_tile_bytes(),               \
                                &Ops<shapes::S>::eval, &Ops<shapes::S>::serve,                 \
-                               ServeLayout<Prec, shapes::S>::WR};                             \
+                               ServeLayout<Prec, shapes::S>::WR, &Ops<shapes::S>::derive,     \
+                               int64_t(sizeof(DerivedConst<typename Prec::T>))};              \
     return &o;                                                                                \
   }
   TDMIX_FOR_EACH_SHAPE(TDMIX_SHAPE_ENTRY)

@@ -58,6 +58,8 @@ struct CtaConst {
   double p[kMaxParams];  // the parameter vector
 };
 
+static_assert(sizeof(CtaConst) % 8 == 0, "copied in 8-byte words");
+
 // d ln kappa / d m0 and d ln kappa / d Gamma0 of resonance r (gradient only):
 // ln kappa = 2 ln m0 + ln Gamma0 - (2L+1)/2 ln q0^2 - 2 ln F_L(z0), z0 = q0^2 r^2,
 // d q0^2 / d m0 = 2 m0 (u^2 - (ma^2 - mb^2)^2) / (4 u^2), u = m0^2, and
@@ -84,6 +86,13 @@ __device__ inline void kappa_log_derivatives(const ModelConst& km, int r, double
   } else {
     cc.dlk_dm[r] = cc.dlk_dg[r] = 0.0;
   }
+}
+
+// Block-wide copy of `bytes` (a multiple of 8) in 8-byte words.
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes) {
+  uint2* d = static_cast<uint2*>(dst);
+  const uint2* q = static_cast<const uint2*>(src);
+  for (int i = threadIdx.x; i < bytes / 8; i += blockDim.x) d[i] = q[i];
 }
 
 // Per-evaluation constants, derived by the kTile threads of a block in
@@ -229,6 +238,36 @@ __device__ inline void derive_compute(const ModelConst& km, CtaConst& cc, BlockC
   }
 }
 
+// The per-evaluation constants of one parameter vector, derived once for a
+// whole batch of evaluations (k_derive) instead of in every block of every
+// evaluation: a block of a batched evaluation copies its record into shared
+// memory, which takes one global-load latency, where deriving the constants
+// takes chains of dependent double-precision operations (about 2 us on this
+// GPU, where each such operation has a latency of ~70 cycles).
+template <class T>
+struct alignas(16) DerivedConst {
+  CtaConst cc;
+  BlockConst<T> bc;
+};
+
+// Block k derives the constants of parameter vector params[k * np ..) into
+// out[k] (the same steps as a k_eval block, with the log-derivatives of
+// kappa).
+template <class P, class S>
+__global__ void __launch_bounds__(kTileEvents) k_derive(const double* __restrict__ params, int np,
+                                                       const __grid_constant__ ModelConst km,
+                                                       DerivedConst<typename P::T>* out) {
+  using T = typename P::T;
+  __shared__ CtaConst cc;
+  __shared__ BlockConst<T> bc;
+  derive_load<T, S::U>(params + size_t(blockIdx.x) * np, nullptr, km, cc, bc);
+  __syncthreads();
+  derive_compute<T, S::U, S::NR, true>(km, cc, bc);
+  __syncthreads();
+  copy_words(&out[blockIdx.x].cc, &cc, sizeof(CtaConst));
+  copy_words(&out[blockIdx.x].bc, &bc, sizeof(BlockConst<T>));
+}
+
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -249,9 +288,39 @@ __device__ __forceinline__ V warp_sum(V a) {
   return a;
 }
 
+// Warp sums of NQ per-lane floats by a butterfly reduce-scatter over groups
+// of 32 values: in the step with offset `off` (16, 8, 4, 2, 1) a lane keeps
+// half of its remaining partial sums (the upper half if bit `off` of its lane
+// index is set), adds the copy lane ^ off holds of them and sends it the
+// other half.  After the five steps lane l holds the warp sum of value l of
+// the group, which it writes to row[l].  31 shuffles per group of 32 values,
+// against 5 per value for one shuffle tree each; the order of the additions
+// is fixed, so the sums are bitwise repeatable.
+template <int NQ>
+__device__ __forceinline__ void warp_sums_butterfly(const float (&vt)[NQ], float* row, int lane) {
+  constexpr int NG = (NQ + 31) / 32;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = g * 32 + i < NQ ? vt[g * 32 + i] : 0.f;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < off; ++i) {
+        const float send = up ? v[i] : v[i + off];
+        const float keep = up ? v[i + off] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+    if (g * 32 + lane < NQ) row[g * 32 + lane] = v[0];
+  }
+}
+
 // Block sum of per-thread values vt[0 .. NQ) into double-float pairs
-// out[q] = (hi, lo), in a fixed order: shuffle trees inside each warp, then
-// the warp sums in warp order.  fp32: everything on the FP32 pipe (TwoSum
+// out[q] = (hi, lo), in a fixed order: inside each warp a butterfly (fp32) or
+// shuffle trees (fp64), then the warp sums in warp order.  fp32: everything on the FP32 pipe (TwoSum
 // across warps); converting each warp sum to double would cost a whole warp
 // instruction on the slow fp64 pipe per value, even for one active lane.
 // fp64: double shuffle trees and sums, rounded to a pair at the end.
@@ -259,10 +328,14 @@ __device__ __forceinline__ V warp_sum(V a) {
 template <class T, int NQ>
 __device__ inline void block_sum_df(const T (&vt)[NQ], T* red, float2* out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if constexpr (sizeof(T) == 4) {
+    warp_sums_butterfly<NQ>(vt, red + warp * NQ, lane);
+  } else {
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const T s = warp_sum(vt[q]);
-    if (lane == 0) red[warp * NQ + q] = s;
+    for (int q = 0; q < NQ; ++q) {
+      const T s = warp_sum(vt[q]);
+      if (lane == 0) red[warp * NQ + q] = s;
+    }
   }
   __syncthreads();
   for (int q = tid; q < NQ; q += blockDim.x) {
@@ -617,7 +690,13 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
     }
   }
   // the parameter loads go out before the other tile copies flood the memory system
-  derive_load<T, U>(a.params, a.hp, a.km, cc, bc);
+  if (a.derived) {  // constants derived once for a batch
+    const auto* rec = static_cast<const DerivedConst<T>*>(a.derived);
+    copy_words(&cc, &rec->cc, sizeof(CtaConst));
+    copy_words(&bc, &rec->bc, sizeof(BlockConst<T>));
+  } else {
+    derive_load<T, U>(a.params, a.hp, a.km, cc, bc);
+  }
   if constexpr (TCG) tc_fence_before_sync();
   __syncthreads();
   uint32_t tmem = 0;
@@ -630,7 +709,7 @@ __global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalA
     for (int64_t k = 1; k < first; ++k) issue(k);
     s_issued = unsigned(first);
   }
-  derive_compute<T, U, NR, GRAD && FULL>(a.km, cc, bc);
+  if (!a.derived) derive_compute<T, U, NR, GRAD && FULL>(a.km, cc, bc);
   __syncthreads();
   if (trace && tid == 0) trace[1] = global_ns();
 

@@ -41,6 +41,11 @@ struct ShapeOps {
   // the persistent serving loop (see serve.cuh)
   cudaError_t (*serve)(int grid, cudaStream_t st, const ServeLoopArgs& a);
   int serve_row_stride;  // float2 entries per chunk-partial row
+  // per-evaluation constants of K parameter vectors (device, K x np) into
+  // `out` (K records of derived_bytes), for the evaluations of a batch
+  // (EvalArgs::derived); null where the path derives them itself
+  cudaError_t (*derive)(int K, const double* params, int np, const ModelConst& km, void* out, cudaStream_t st);
+  int64_t derived_bytes;
 };
 
 // Launcher of the runtime-table evaluation (generic.cu) for model

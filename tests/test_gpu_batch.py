@@ -41,6 +41,13 @@ def test_batch_matches_oracle_and_single_calls(name, nd, nm, wid, precision):
     c.nll_batch(Pd, out2, grad2)
     torch.cuda.synchronize()
     assert torch.equal(out, out2) and torch.equal(grad, grad2)
+    # a longer batch (its constants records are reallocated) repeats the first six points bitwise
+    P10 = np.concatenate([P, _points(m, 4, 400 + wid)])
+    out10 = torch.empty(10, dtype=torch.float64, device=dev)
+    grad10 = torch.empty(10, n_p, dtype=torch.float64, device=dev)
+    c.nll_batch(torch.from_numpy(P10).to(dev), out10, grad10)
+    torch.cuda.synchronize()
+    assert torch.equal(out10[:6], out) and torch.equal(grad10[:6], grad)
     v_b, g_b = out.cpu().numpy(), grad.cpu().numpy()
     for k in range(6):
         v0, g0 = tdamp.nll_and_grad(m, torch.from_numpy(data), torch.from_numpy(t), torch.from_numpy(mc), P[k])
