@@ -822,6 +822,82 @@ def toy_study(precision, sizes, mc, p0, label):
             "loop": {k: st[k] for k in ("launches", "abnormal_exits", "published", "last_exit_status")}}
 
 
+def serving_throughput(mc, p0, precision="fp32", n_samples=64, n_events=100_000, rounds=40, clients=16,
+                       per_client=4):
+    """The device-resident serving loop at steady state: n_samples generated
+    samples of n_events (model fixed) are made resident by one request each,
+    then `clients` threads each keep `per_client` requests in flight (submit
+    for all of their samples, then wait for all) for `rounds` rounds, at
+    parameter points with the coefficients and x, y moved.  Reports evals/s,
+    event-evaluations/s, p50/p99 latency from the server's statistics, and the
+    single-context cached pass (one evaluation per call with device
+    parameters) on one of the same samples for comparison."""
+    import torch
+    from paper_1702_06735_gb300.tdmix import TDMix, TDMixServer
+    srv = TDMixServer(MODEL, precision, hbm_budget_bytes=8 << 30, max_slots=256)
+    try:
+        srv.add_mc(mc)
+        ids = [srv.add_generated_sample(p0, n_events, KEY0 + 6, STREAM_TOY0 + 5000 + k) for k in range(n_samples)]
+        nc = model_sizes()[0]
+        move = np.zeros(len(p0), dtype=bool)
+        move[2:2 * nc] = True
+        move[-2:] = True
+        for sid in ids:                       # admission (generation + component cache)
+            srv.evaluate(sid, p0, timeout_s=600.0)
+        mine = [ids[c::clients] for c in range(clients)]
+
+        def client(c):
+            for r in range(rounds):
+                for q in range(0, len(mine[c]), per_client):
+                    group = mine[c][q:q + per_client]
+                    tickets = [srv.submit(sid, step_params(p0, move, 97 * r + sid)) for sid in group]
+                    for tk in tickets:
+                        srv.wait(tk, timeout_s=600.0)
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        with cf_pool(clients) as ex:
+            list(ex.map(client, range(clients)))
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    finally:
+        srv.close()
+    evals = n_samples * rounds
+    # the single-context cached pass on one sample of the same size
+    g = TDMix(MODEL, "fp64")
+    d, t, _ = generate(g, n_events, 6, STREAM_TOY0 + 5000, params=p0)
+    g.close()
+    c, _ = load(MODEL, precision, d, t, mc)
+    mask = np.zeros(len(p0), dtype=np.int32)
+    mask[2:2 * nc] = 1
+    mask[-2:] = 1
+    c.set_floating(mask)
+    c.nll(p0)                                 # component cache and MC sums at the fixed model
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K = 200
+    P = torch.from_numpy(np.stack([step_params(p0, move, k) for k in range(K)])).to(dev)
+    out = torch.empty(K, dtype=torch.float64, device=dev)
+    grad = torch.empty(K, len(p0), dtype=torch.float64, device=dev)
+    c.nll(step_params(p0, move, 1))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for k in range(K):
+        c.nll_device(P[k], out[k:k + 1], grad[k])
+    torch.cuda.synchronize()
+    single = K / (time.perf_counter() - t1)
+    c.close()
+    return {"workload": f"{MODEL}, {n_samples} resident generated samples of {n_events} events, model fixed, "
+                        f"coefficients and x, y moved; {clients} clients with {per_client} requests in flight each",
+            "evals": evals, "wall_s": wall, "evals_per_s": evals / wall, "event_evals_per_s": evals * n_events / wall,
+            "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+            "single_context_cached": {"evals_per_s": single, "event_evals_per_s": single * n_events,
+                                      "note": "one tdmix_nll call per evaluation, device parameters, same sample size"}}
+
+
+def cf_pool(n):
+    import concurrent.futures as cf
+    return cf.ThreadPoolExecutor(max_workers=n)
+
+
 def sensitivity(mc, p0, n_toys, sizes=(20_000, 50_000, 70_000)):
     """The sensitivity study of Sec. 4: for each sample size, n_toys
     pseudo-experiments of the fixed model at the world-average x, y, fitted
@@ -933,6 +1009,8 @@ def run_tdmix(args):
                 if args.toys_fp64 > 0:
                     studies["toy_study"]["fp64"] = toy_study("fp64", sizes[:args.toys_fp64], mc2, p0,
                                                              lab + f"; the first {args.toys_fp64} toys")
+            studies["serving_throughput"] = {"fp32": serving_throughput(mc2, p0, "fp32"),
+                                             "fp64": serving_throughput(mc2, p0, "fp64", rounds=10)}
             if args.sensitivity > 0:
                 studies["sensitivity"] = sensitivity(mc2, p0, args.sensitivity)
             del mc2

@@ -40,8 +40,14 @@ struct ServeLayout {
   // (the bulk copy of a request's rows needs both)
   static constexpr int WR = (WD + 1) & ~1;
   static constexpr int stage_bytes = 2 * U * kTile * int(sizeof(T)) + kTile * 8;
+  // stages of the tile ring: as many as fit 160 KiB, 2 to 6 (a chunk's
+  // tiles stream from HBM; the lookahead covers the copy latency)
+  static constexpr int stages() {
+    const int n = 160 * 1024 / stage_bytes;
+    return n < 2 ? 2 : (n > 6 ? 6 : n);
+  }
   static constexpr int smem_bytes() {
-    const int st = 2 * stage_bytes, pr = kServeMaxChunks * WR * 8;
+    const int st = stages() * stage_bytes, pr = kServeMaxChunks * WR * 8;
     return st > pr ? st : pr;
   }
 };
@@ -68,8 +74,9 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
   using LY = ServeLayout<P, S>;
   constexpr int U = S::U, NR = S::NR, WD = LY::WD, WR = LY::WR, TE = kTile, ES = int(sizeof(T));
   constexpr int WMC = Layout<P, S>::WMC;
+  constexpr int NST = LY::stages();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[3];
+  __shared__ __align__(8) uint64_t bars[NST + 1];  // one per stage, then the row copy's
   __shared__ CtaConst cc;
   __shared__ BlockConst<T> bc;
   __shared__ T red[(kTile / 32) * (2 + 4 * U)];
@@ -84,7 +91,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
   __shared__ unsigned s_last;
   __shared__ ServeSlot s_req;  // the request's fields (one read of mapped memory)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned char* stage[2] = {smem_raw, smem_raw + LY::stage_bytes};
+  auto stage = [&](int st) { return smem_raw + st * LY::stage_bytes; };
   for (int j = tid; j < kLogTable; j += blockDim.x) {
     const double2 v = static_cast<const double2*>(a.logtab)[j];
     logtab[j] = v;
@@ -94,13 +101,12 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
     }
   }
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int q = 0; q < NST; ++q) mbar_init(&bars[q], 1);
     mbar_fence_init();
   }
   __syncthreads();
   const int np = a.km.n_params, nc = a.km.n_chains;
-  uint32_t uses = 0;                    // completed stage phases (both stages), for parity tracking
+  uint32_t uses = 0;                    // stage uses so far: stage uses % NST, phase parity (uses / NST) & 1
   unsigned long long cursor = a.head;   // thread 0: next entry to try
   float2* part_all = static_cast<float2*>(a.part);
 
@@ -167,16 +173,14 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
     const int ntl = t1 - t0;
     const void* cache = s_req.cache;
     const int64_t tile_bytes = s_req.tile_bytes, n_ev = s_req.n;
-    auto issue = [&](int j, uint32_t use) {  // tile t0 + j into stage use & 1 (one bulk copy)
-      const int st = int(use & 1);
+    auto issue = [&](int j, uint32_t use) {  // tile t0 + j into stage use % NST (one bulk copy)
+      const int st = int(use % NST);
       mbar_arrive_expect_tx(&bars[st], uint32_t(tile_bytes));
-      bulk_g2s(stage[st], static_cast<const unsigned char*>(cache) + int64_t(t0 + j) * tile_bytes,
+      bulk_g2s(stage(st), static_cast<const unsigned char*>(cache) + int64_t(t0 + j) * tile_bytes,
                uint32_t(tile_bytes), &bars[st]);
     };
-    if (tid == 0) {
-      issue(0, uses);
-      if (ntl > 1) issue(1, uses + 1);
-    }
+    if (tid == 0)
+      for (int q = 0; q < NST && q < ntl; ++q) issue(q, uses + q);
     derive_load<T, U>(a.slots[slot].params, nullptr, a.km, cc, bc);
     __syncthreads();
     derive_compute<T, U, NR>(a.km, cc, bc);
@@ -191,8 +195,8 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
 #pragma unroll
     for (int j = 0; j < U; ++j) gAr[j] = gAi[j] = gBr[j] = gBi[j] = 0;
     for (int j = 0; j < ntl; ++j, ++uses) {
-      const int st = int(uses & 1);
-      const bool ok = mbar_wait_bounded(&bars[st], (uses >> 1) & 1u, kWaitNs);
+      const int st = int(uses % NST);
+      const bool ok = mbar_wait_bounded(&bars[st], (uses / NST) & 1u, kWaitNs);
       if (__syncthreads_or(!ok)) {
         failed = true;
         failed_at = j;
@@ -200,9 +204,9 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
       }
       const int64_t i = int64_t(t0 + j) * TE + tid;
       if (i < n_ev) {
-        const T* sbase = reinterpret_cast<const T*>(stage[st]);
+        const T* sbase = reinterpret_cast<const T*>(stage(st));
         // decay time: a double (fp64 path) or a double-float pair (fp32 path)
-        const unsigned char* tplane = stage[st] + 2 * U * TE * ES;
+        const unsigned char* tplane = stage(st) + 2 * U * TE * ES;
         const double t_e = P::kF32 ? 0.0 : reinterpret_cast<const double*>(tplane)[tid];
         const float2 t_f = P::kF32 ? reinterpret_cast<const float2*>(tplane)[tid] : float2{0.f, 0.f};
         EventCore<P, S> ev;
@@ -234,16 +238,17 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
         }
       }
       __syncthreads();
-      if (tid == 0 && j + 2 < ntl) issue(j + 2, uses + 2);
+      if (tid == 0 && j + NST < ntl) issue(j + NST, uses + NST);
     }
     if (failed) {
-      // the copies of tiles failed_at and failed_at + 1 (if any) are in
-      // flight: let them land before shared memory is reused, and count
-      // their stage phases
-      const uint32_t in_flight = ntl - failed_at > 1 ? 2u : 1u;
+      // the copies of tiles failed_at .. failed_at + NST - 1 (those that
+      // exist) are in flight: let them land before shared memory is
+      // reused, and count their stage phases
+      const uint32_t in_flight = uint32_t(ntl - failed_at < NST ? ntl - failed_at : NST);
       if (tid == 0) {
         atomicOr(a.status, 1);
-        for (uint32_t u = uses; u < uses + in_flight; ++u) mbar_wait_bounded(&bars[u & 1], (u >> 1) & 1u, kWaitNs);
+        for (uint32_t u = uses; u < uses + in_flight; ++u)
+          mbar_wait_bounded(&bars[u % NST], (u / NST) & 1u, kWaitNs);
       }
       __syncthreads();
       uses += in_flight;
@@ -293,14 +298,14 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
     const int nch = s_req.n_chunks;
     if (tid == 0) {
       asm volatile("fence.proxy.async.global;" ::: "memory");
-      mbar_init(&bars[2], 1);
+      mbar_init(&bars[NST], 1);
       mbar_fence_init();
       const uint32_t bytes = uint32_t(nch) * uint32_t(WR) * 8u;  // a multiple of 16
-      mbar_arrive_expect_tx(&bars[2], bytes);
-      bulk_g2s(sp, part, bytes, &bars[2]);  // 16-byte aligned
+      mbar_arrive_expect_tx(&bars[NST], bytes);
+      bulk_g2s(sp, part, bytes, &bars[NST]);  // 16-byte aligned
     }
     __syncthreads();
-    const bool ok = mbar_wait_bounded(&bars[2], 0, kWaitNs);
+    const bool ok = mbar_wait_bounded(&bars[NST], 0, kWaitNs);
     if (__syncthreads_or(!ok) && tid == 0) atomicOr(a.status, 1);
     for (int v = tid; v < WMC; v += blockDim.x) colsum[v] = a.mc_cols[v];
     for (int v = tid; v < WD; v += blockDim.x) {
