@@ -24,6 +24,10 @@ Sec. 3) the reading used here is stated in the docstring:
   the exchange of the two identical pi- (no 1/sqrt 2).
 * normalisation: phase space by the mean over the Monte Carlo sample, decay
   time by the closed-form integrals over [0, inf).
+* decay-time resolution (an extension; the paper's study has none, Sec. 4):
+  when the model file gives "time_resolution" sigma, the rate is folded with
+  a Gaussian of width sigma in the measured time, which ranges over the real
+  line, so the normalisation is unchanged (rate_resolved).
 """
 from __future__ import annotations
 
@@ -75,6 +79,7 @@ class Model:
     x: float
     y: float
     float_xy: bool
+    sigma_t: float = 0.0   # Gaussian decay-time resolution (ps); 0: none
     resonances: list = field(default_factory=list)
     chains: list = field(default_factory=list)
 
@@ -125,7 +130,8 @@ def load_model(src) -> Model:
     m = Model(parent_mass=d["parent_mass"], masses=[p["mass"] for p in d["final_state"]],
               tau=d["tau"], r_res=d["r_resonance"], r_parent=d["r_parent"],
               bose=tuple(d["bose_swap"]) if d.get("bose_swap") else None,
-              x=d["x"], y=d["y"], float_xy=d.get("float_xy", True))
+              x=d["x"], y=d["y"], float_xy=d.get("float_xy", True),
+              sigma_t=float(d.get("time_resolution", 0.0)))
     for r in d["resonances"]:
         m.resonances.append(Resonance(r["name"], r["mass"], r["width"], r["shape"], r.get("L", 0),
                                       tuple(r.get("daughter_masses", (0.0, 0.0))),
@@ -358,11 +364,48 @@ def normalisation(model: Model, mc_events, params, mc_weights=None):
 
 
 def event_rates(model: Model, events, t, params):
-    """Unnormalised rate e^{-Gamma t} B(e) of Eq. (mix) per event."""
+    """Unnormalised rate e^{-Gamma t} B(e) of Eq. (mix) per event (folded
+    with the decay-time resolution when the model has one)."""
     _, _, _, x, y = _unpack(model, params)
     A, Ab = amplitudes(model, events, params)
+    if model.sigma_t > 0:
+        return rate_resolved(A, Ab, t, x, y, model.gamma, model.sigma_t)
     R, _ = rate_literal(A, Ab, t, x, y, model.gamma)
     return R
+
+
+# ----------------------------------------------------------------------------
+# Decay-time resolution: an extension the paper leaves out (its study has no
+# resolution, Sec. 4).  Reading: the measured time is the true time plus a
+# Gaussian of fixed width sigma, measured times range over the whole real
+# line, so the normalisation (the time integral of the rate) is unchanged.
+# ----------------------------------------------------------------------------
+_GL_ORDER = 192
+_GL_CACHE = {}
+
+
+def _gauss_legendre(n: int):
+    if n not in _GL_CACHE:
+        import numpy as np
+        xg, wg = np.polynomial.legendre.leggauss(n)
+        _GL_CACHE[n] = (torch.tensor(xg, dtype=F64), torch.tensor(wg, dtype=F64))
+    return _GL_CACHE[n]
+
+
+def rate_resolved(A, Ab, t, x, y, gamma, sigma):
+    """R(t) = int_0^inf dt' e^{-Gamma t'} B(t') G(t - t'; sigma), G the
+    normal density of width sigma and B of Eq. (mix) (rate_literal), by
+    Gauss-Legendre quadrature over t' in [max(0, t - 12 sigma), t + 12 sigma]
+    (beyond 12 sigma the Gaussian is below 1e-31 of its peak)."""
+    t = torch.as_tensor(t, dtype=F64)
+    xg, wg = _gauss_legendre(_GL_ORDER)
+    lo = torch.clamp(t - 12 * sigma, min=0.0)
+    hi = torch.clamp(t + 12 * sigma, min=0.0)
+    half, mid = (hi - lo) / 2, (hi + lo) / 2
+    tp = mid[:, None] + half[:, None] * xg[None, :]
+    R0, _ = rate_literal(A[:, None], Ab[:, None], tp, x, y, gamma)
+    g = torch.exp(-(t[:, None] - tp) ** 2 / (2 * sigma * sigma)) / (sigma * math.sqrt(2 * math.pi))
+    return (R0 * g * wg[None, :]).sum(dim=1) * half
 
 
 def nll(model: Model, data_events, data_t, mc_events, params, mc_weights=None):
