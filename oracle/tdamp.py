@@ -24,6 +24,10 @@ Sec. 3) the reading used here is stated in the docstring:
   the exchange of the two identical pi- (no 1/sqrt 2).
 * normalisation: phase space by the mean over the Monte Carlo sample, decay
   time by the closed-form integrals over [0, inf).
+* background (an extension; the paper's study has none, Sec. 4): when the
+  model file gives "background": {"fraction": f, "tau": tau_b}, each data
+  event's density is (1 - f) R / N + f B, B flat in the normalised phase
+  space (volume 1: the MC mean) and e^{-t/tau_b}/tau_b in time.
 * decay-time resolution (an extension; the paper's study has none, Sec. 4):
   when the model file gives "time_resolution" sigma, the rate is folded with
   a Gaussian of width sigma in the measured time, which ranges over the real
@@ -80,6 +84,8 @@ class Model:
     y: float
     float_xy: bool
     sigma_t: float = 0.0   # Gaussian decay-time resolution (ps); 0: none
+    bkg_fraction: float = 0.0  # fraction of background events; 0: none
+    bkg_tau: float = 1.0       # background lifetime (ps)
     resonances: list = field(default_factory=list)
     chains: list = field(default_factory=list)
 
@@ -131,7 +137,9 @@ def load_model(src) -> Model:
               tau=d["tau"], r_res=d["r_resonance"], r_parent=d["r_parent"],
               bose=tuple(d["bose_swap"]) if d.get("bose_swap") else None,
               x=d["x"], y=d["y"], float_xy=d.get("float_xy", True),
-              sigma_t=float(d.get("time_resolution", 0.0)))
+              sigma_t=float(d.get("time_resolution", 0.0)),
+              bkg_fraction=float((d.get("background") or {}).get("fraction", 0.0)),
+              bkg_tau=float((d.get("background") or {}).get("tau", 1.0)))
     for r in d["resonances"]:
         m.resonances.append(Resonance(r["name"], r["mass"], r["width"], r["shape"], r.get("L", 0),
                                       tuple(r.get("daughter_masses", (0.0, 0.0))),
@@ -408,10 +416,34 @@ def rate_resolved(A, Ab, t, x, y, gamma, sigma):
     return (R0 * g * wg[None, :]).sum(dim=1) * half
 
 
+def background_density(model: Model, t):
+    """Density of a background event per unit of normalised phase space and
+    of (measured) decay time: flat in phase space, e^{-t/tau_b} / tau_b in
+    the true time (folded with the resolution when the model has one, by the
+    same quadrature as rate_resolved)."""
+    t = torch.as_tensor(t, dtype=F64)
+    tb = model.bkg_tau
+    if model.sigma_t <= 0:
+        return torch.where(t >= 0, torch.exp(-torch.clamp(t, min=0.0) / tb) / tb, torch.zeros_like(t))
+    sigma = model.sigma_t
+    xg, wg = _gauss_legendre(_GL_ORDER)
+    lo = torch.clamp(t - 12 * sigma, min=0.0)
+    hi = torch.clamp(t + 12 * sigma, min=0.0)
+    half, mid = (hi - lo) / 2, (hi + lo) / 2
+    tp = mid[:, None] + half[:, None] * xg[None, :]
+    g = torch.exp(-(t[:, None] - tp) ** 2 / (2 * sigma * sigma)) / (sigma * math.sqrt(2 * math.pi))
+    return (torch.exp(-tp / tb) / tb * g * wg[None, :]).sum(dim=1) * half
+
+
 def nll(model: Model, data_events, data_t, mc_events, params, mc_weights=None):
-    """-sum_e ln( R(e) / N ) over the data sample."""
+    """-sum_e ln( R(e) / N ) over the data sample; with a background
+    fraction f (an extension; the paper's study has no background, Sec. 4),
+    -sum_e ln( (1 - f) R(e) / N + f B(e) ), B the background density."""
     R = event_rates(model, data_events, data_t, params)
     N = normalisation(model, mc_events, params, mc_weights)
+    if model.bkg_fraction > 0:
+        f = model.bkg_fraction
+        return -torch.log((1 - f) * R / N + f * background_density(model, data_t)).sum()
     return -(torch.log(R) - torch.log(N)).sum()
 
 
