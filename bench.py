@@ -893,6 +893,37 @@ def serving_throughput(mc, p0, precision="fp32", n_samples=64, n_events=100_000,
                                       "note": "one tdmix_nll call per evaluation, device parameters, same sample size"}}
 
 
+def floating_model_toys(n_toys=100, n_events=20_000):
+    """Pseudo-experiments fitted with the model floating (every resonance mass
+    and width, x and y; the coefficients fixed), an extension of the paper's
+    fixed-model study (Sec. 4), on the 2-chain model; the same
+    events are also fitted with the model fixed.  Reports pulls and the
+    growth of the x, y errors when the model floats."""
+    from paper_1702_06735_gb300 import toys
+    from paper_1702_06735_gb300.tdmix import TDMix
+    c = TDMix(MODEL_2CHAIN, "fp64")
+    gen = c.default_params()
+    mc, _, _ = generate(c, 1_000_000, 7, STREAM_MC, flat=True, with_times=False)
+    c.close()
+    t0 = time.perf_counter()
+    fits = toys.run_floating(MODEL_2CHAIN, "fp64", [n_events] * n_toys, gen, mc, seed=KEY0 + 7,
+                             stream0=STREAM_TOY0, compare_fixed=True)
+    wall = time.perf_counter() - t0
+    nc = model_sizes(MODEL_2CHAIN)[0]
+    out = {"workload": f"{MODEL_2CHAIN}: {n_toys} toys of {n_events} events generated on the device, 1,000,000 MC; "
+                       "fits with the model floating and, on the same events, with the model fixed",
+           "precision": "fp64 (Hessian errors from finite differences of the gradient)",
+           "converged": sum(f.converged for f in fits), "wall_s": wall,
+           "evals": sum(f.n_eval for f in fits)}
+    for name, idx in (("x", len(gen) - 2), ("y", len(gen) - 1), ("kstar_mass", 2 * nc), ("kstar_width", 2 * nc + 1)):
+        out[name] = toys.floating_pulls(fits, gen, idx)
+    ok = [f for f in fits if f.converged and f.xy_fixed_model and np.isfinite(f.xy_fixed_model[2])]
+    out["xy_error_ratio_floating_over_fixed"] = {
+        "x": float(np.median([f.errors[-2] / f.xy_fixed_model[2] for f in ok])),
+        "y": float(np.median([f.errors[-1] / f.xy_fixed_model[3] for f in ok]))}
+    return out
+
+
 def cf_pool(n):
     import concurrent.futures as cf
     return cf.ThreadPoolExecutor(max_workers=n)
@@ -996,6 +1027,7 @@ def run_tdmix(args):
         studies["config3_precision"] = config3_precision(dev, stream, peak)
         studies["config4_gradient_fit"] = config4_gradient_fit(dev, stream)
         studies["paper_fit_benchmark"] = paper_fit_benchmark(dev, stream)
+        studies["floating_model_toys"] = floating_model_toys()
         if args.toys > 0 or args.sensitivity > 0:
             gm = TDMix(MODEL, "fp64")
             mc2, _, _ = generate(gm, 2_000_000, 5, STREAM_MC, flat=True, with_times=False)

@@ -113,7 +113,22 @@ typedef struct {
  * returns TDMIX_ERR_UNSUPPORTED) or the device generator (tdmix_generate
  * returns TDMIX_ERR_UNSUPPORTED).  tdmix_kernel_path tells which kernels a
  * context uses; precision | TDMIX_GENERIC selects the runtime-table kernels
- * for any model. */
+ * for any model.
+ * A model file may give "time_resolution": sigma (ps), a Gaussian
+ * decay-time resolution (an extension; the paper's study has none, Sec. 4).
+ * The rate of Eq. (mix) is then folded with it in the measured time t
+ * (which may be negative): R(t) = int_0^inf e^{-Gamma t'} B(t') G(t - t';
+ * sigma) dt', in closed form through the Faddeeva function; N is unchanged;
+ * the NLL is -sum ln(R/N).  Such a model always runs on the runtime-table
+ * kernels; |x| Gamma sigma / sqrt 2 must not exceed 0.25 (TDMIX_ERR_DOMAIN);
+ * tdmix_generate smears the accepted true times by the resolution.
+ * A model file may also give "background": {"fraction": f, "tau": tau_b}
+ * (an extension; the paper's study has none, Sec. 4): each data event's
+ * density is then (1 - f) R / N + f B, B flat in the normalised phase space
+ * (the MC mean has volume 1) and e^{-t/tau_b}/tau_b in the decay time
+ * (folded with the resolution if there is one), and the NLL is -sum ln of
+ * it.  Also runtime-table kernels only (three passes: MC, N, data);
+ * tdmix_event_rates still returns the signal rates R and N. */
 int tdmix_create(const char* model_json, int precision, tdmix_ctx** out);
 
 /* The kernels the context evaluates with (tdmix_kernel_path_kind), or a

@@ -174,6 +174,9 @@ ModelConst make_model_const(const CompiledModel& m, const std::vector<int>& floa
   k.r_res = m.r_res;
   k.gamma = 1.0 / m.tau;
   k.tau = m.tau;
+  k.sigma_t = m.sigma_t;
+  k.bkg_fraction = m.bkg_fraction;
+  k.bkg_tau = m.bkg_tau;
   for (size_t r = 0; r < m.res.size(); ++r) {
     k.res_ma[r] = m.res[r].ma;
     k.res_mb[r] = m.res[r].mb;
@@ -211,6 +214,7 @@ ShapeOps make_generic_ops(const CompiledModel& m) {
   o.serve_row_stride = 0;
   o.derive = nullptr;
   o.derived_bytes = 0;
+  o.cached_blocks = 1;
   return o;
 }
 
@@ -242,6 +246,8 @@ int check_params(tdmix_ctx* ctx, const double* p) {
       return fail(ctx, TDMIX_ERR_DOMAIN, "resonance '" + m.res[r].name + "' needs a positive mass and width");
   }
   if (!(std::fabs(p[np - 1]) < 1.0)) return fail(ctx, TDMIX_ERR_DOMAIN, "|y| must be below 1");
+  if (m.sigma_t > 0 && !(std::fabs(p[np - 2]) * m.sigma_t / (m.tau * std::sqrt(2.0)) <= kMaxResolutionMix))
+    return fail(ctx, TDMIX_ERR_DOMAIN, "|x| Gamma sigma_t / sqrt 2 must not exceed 0.25 with a decay-time resolution");
   return TDMIX_OK;
 }
 
@@ -430,7 +436,12 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   }
   int rc;
   const int64_t items = ctx->data.dev.n_tiles + (full && !data_only ? ctx->mc.dev.n_tiles : 0);
-  const int cap = grid_cap > 0 && grid_cap < ctx->num_sms ? grid_cap : ctx->num_sms;
+  // the cached pass may run several blocks per SM (ShapeOps::cached_blocks)
+  // when every block gets several tiles; on fewer tiles the per-block fixed
+  // costs (constants, block sums, the last block's column sums over more
+  // rows) outweigh the latency hidden by the extra warps
+  const int per_sm = full || items < int64_t(4) * ctx->ops->cached_blocks * ctx->num_sms ? 1 : ctx->ops->cached_blocks;
+  const int cap = grid_cap > 0 && grid_cap < per_sm * ctx->num_sms ? grid_cap : per_sm * ctx->num_sms;
   const int grid = int(items < cap ? items : cap);
   // parameters travel in the kernel arguments (host callers) or are read
   // from the caller's device array
@@ -442,7 +453,9 @@ int enqueue_eval(tdmix_ctx* ctx, const double* params, bool host_params, bool wa
   if (host_params) std::memcpy(a.hp, params, np * sizeof(double));
   else a.params = params;
   a.part = ctx->d_part;
-  a.ld = ctx->num_sms;
+  // rows of the partial array the kernel may stage in shared memory: a full
+  // evaluation reserves room for one per SM; a cached pass only for its grid
+  a.ld = full ? ctx->num_sms : grid;
   a.gram_store = ctx->d_gram;
   a.counter = ctx->d_counter;
   a.rates = rates;
@@ -589,7 +602,9 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
     return TDMIX_ERR_ARG;
   }
   ctx->f32 = precision == TDMIX_FP32;
-  ctx->ops = force_generic ? nullptr : find_shape_ops(ctx->model.signature(), ctx->f32);
+  // a decay-time resolution and a background are evaluated by the runtime-table kernels only
+  const bool extension = ctx->model.sigma_t > 0 || ctx->model.bkg_fraction > 0;
+  ctx->ops = force_generic || extension ? nullptr : find_shape_ops(ctx->model.signature(), ctx->f32);
   *out = ctx;
   if (!ctx->ops) {
     // no specialisation of this structure: the runtime-table kernels, in fp64
@@ -612,7 +627,8 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out) {
   TDMIX_CK(cudaMalloc(&ctx->d_gram, (1 + 2 * kMaxComp * kMaxComp + 2 * kMaxRes) * sizeof(double)));
   TDMIX_CK(cudaMalloc(&ctx->d_sumt, sizeof(double)));
   // block partial rows [num_sms][width] (+16 bytes: copied in whole 16-byte units)
-  TDMIX_CK(cudaMalloc(&ctx->d_part, size_t(ctx->num_sms) * (ctx->ops->mc_width + ctx->ops->data_width) * 8 + 16));
+  TDMIX_CK(cudaMalloc(&ctx->d_part, size_t(kCachedBlocksPerSM) * ctx->num_sms *
+                                         (ctx->ops->mc_width + ctx->ops->data_width) * 8 + 16));
   TDMIX_CK(cudaMalloc(&ctx->d_counter, sizeof(unsigned)));
   TDMIX_CK(cudaMalloc(&ctx->d_ranges, (ctx->num_sms + 1) * sizeof(int64_t)));
   TDMIX_CK(cudaMalloc(&ctx->d_zero_ranges, (ctx->num_sms + 1) * sizeof(int64_t)));
@@ -1007,8 +1023,10 @@ int tdmix_test_withhold_copy(tdmix_ctx* ctx, int enable) {
 int tdmix_trace(tdmix_ctx* ctx, int enable) {
   if (!ctx) return TDMIX_ERR_ARG;
   if (enable && !ctx->d_trace) {
-    TDMIX_CK(cudaMalloc(&ctx->d_trace, size_t(ctx->num_sms) * kTracePhases * sizeof(unsigned long long)));
-    TDMIX_CK(cudaMemset(ctx->d_trace, 0, size_t(ctx->num_sms) * kTracePhases * sizeof(unsigned long long)));
+    // room for every block of a cached pass (kCachedBlocksPerSM per SM); the first num_sms are read back
+    const size_t n = size_t(kCachedBlocksPerSM) * ctx->num_sms * kTracePhases;
+    TDMIX_CK(cudaMalloc(&ctx->d_trace, n * sizeof(unsigned long long)));
+    TDMIX_CK(cudaMemset(ctx->d_trace, 0, n * sizeof(unsigned long long)));
   } else if (!enable && ctx->d_trace) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->d_trace);

@@ -35,11 +35,22 @@ constexpr int kMaxParams = 2 * kMaxChains + 2 * kMaxRes + 2;
 struct ModelConst {
   int n_chains, n_params;
   double r_res, gamma, tau;  // tau = 1 / gamma
+  double sigma_t;            // Gaussian decay-time resolution (0: none; generic evaluation only)
+  double bkg_fraction, bkg_tau;  // background fraction (0: none) and lifetime (generic evaluation only)
   double res_ma[kMaxRes], res_mb[kMaxRes];
   int8_t res_shape[kMaxRes], res_L[kMaxRes];
   int8_t chain_comp[kMaxChains], chain_amp[kMaxChains];
   uint8_t floating[kMaxParams];
 };
+
+// Largest |x| Gamma sigma_t / sqrt 2 the folded rate accepts (the real part
+// of the Faddeeva argument; the evaluation is verified up to 0.3).
+constexpr double kMaxResolutionMix = 0.25;
+
+// Blocks per SM of the cached pass (component cache in, no MC tiles): its
+// registers (~113 per thread) and a ring of at most 88 KiB allow two, which
+// doubles the warps that hide the latency of its short per-event work.
+constexpr int kCachedBlocksPerSM = 2;
 
 // Events per tile: the unit of every bulk copy and of the static work
 // assignment; one event per consumer thread.

@@ -171,7 +171,7 @@ const ShapeOps* TDMIX_FIND(const std::string& sig) {
                                LY_::mc_tile_bytes(true), LY_::cache_tile_bytes(),               \
                                &Ops<shapes::S>::eval, &Ops<shapes::S>::serve,                 \
                                ServeLayout<Prec, shapes::S>::WR, &Ops<shapes::S>::derive,     \
-                               int64_t(sizeof(DerivedConst<typename Prec::T>))};              \
+                               int64_t(sizeof(DerivedConst<typename Prec::T>)), LY_::cached_blocks}; \
     return &o;                                                                                \
   }
   TDMIX_FOR_EACH_SHAPE(TDMIX_SHAPE_ENTRY)

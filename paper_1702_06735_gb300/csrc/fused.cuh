@@ -46,6 +46,10 @@ constexpr int kTile = kTileEvents;
 constexpr int kWarps = kTile / 32;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 constexpr int kStageBudget = 192 * 1024;     // shared memory for the tile ring
+// The cached pass (component cache in, no MC tiles) runs kCachedBlocksPerSM
+// blocks per SM: its ring gets under half the budget, so that both blocks'
+// shared memory fits.
+constexpr int kStageBudgetCached = 88 * 1024;
 
 // Per-evaluation constants in double precision (shared memory of a block).
 struct CtaConst {
@@ -380,8 +384,12 @@ struct Layout {
   }
   // ring depth: as many stages as fit the budget, 2 to 6 (the lookahead must
   // cover the memory latency under full load, a few microseconds)
+  // blocks per SM of the cached pass: kCachedBlocksPerSM on the fp32 path up to
+  // 8 components (within 128 registers), else one
+  static constexpr int cached_blocks = (P::kF32 && U <= 8) ? kCachedBlocksPerSM : 1;
   static constexpr int stages(bool full) {
-    const int n = (kStageBudget - extra_bytes(full)) / stage_bytes(full);
+    const int budget = full || cached_blocks == 1 ? kStageBudget : kStageBudgetCached;
+    const int n = (budget - extra_bytes(full)) / stage_bytes(full);
     return n < 2 ? 2 : (n > 6 ? 6 : n);
   }
   // bytes of one tile in global memory (SampleDev::tile_bytes / cache_tile_bytes)
@@ -579,7 +587,8 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
 // tolerance) and do not carry the recomputation's code.
 // GRAM: how the MC normalisation matrix is accumulated (GramMode).
 template <class P, class S, bool FULL, bool GRAD, bool WEIGHTED, bool RATES = false, int GRAM = kGramRegs>
-__global__ void __launch_bounds__(kTile, 1) k_eval(const __grid_constant__ EvalArgs a) {
+__global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_blocks)
+    k_eval(const __grid_constant__ EvalArgs a) {
   using T = typename P::T;
   using LY = Layout<P, S, GRAM>;
   static_assert(GRAM != kGramTensor || P::kF32, "tensor-core normalisation matrix on the fp32 path");

@@ -12,7 +12,9 @@
 // precision whatever precision the context was created with.  Per-event
 // arrays indexed through the tables live in thread-local memory, so this
 // path is several times slower than a specialised one; it lets a user
-// compose a model (Sec. 3) without rebuilding the library.
+// compose a model (Sec. 3) without rebuilding the library.  It also
+// evaluates models with a decay-time resolution (resolution.cuh), an
+// extension the paper leaves out.
 //
 // Two launches per evaluation, on the planes the kinematic precompute wrote
 // (fp64 tile-major layout of SampleDev):
@@ -31,6 +33,7 @@
 
 #include "fused.cuh"
 #include "kernels.hpp"
+#include "resolution.cuh"
 
 namespace tdmix {
 namespace {
@@ -252,7 +255,10 @@ __device__ void block_columns(int nq, F v, double* red, double* out) {
   __syncthreads();
 }
 
-template <bool GRAD>
+// PASS 0: MC and data tiles; with a background the data pass needs N first:
+// PASS 1 runs the MC tiles only, k_generic_norm forms N, and PASS 2 the data
+// tiles (each event's density (1 - f) R / N + f B_bkg).
+template <bool GRAD, int PASS>
 __global__ void __launch_bounds__(kGT, 1) k_generic_tiles(const __grid_constant__ EvalArgs a) {
   __shared__ GConst g;
   __shared__ double red[kGW * kMaxWD];
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kGT, 1) k_generic_tiles(const __grid_constant_
   const SampleDev& dd = a.data;
 
   // ---- MC tiles: normalisation sums and the adjoint of the time-integrated rate
-  {
+  if (PASS != 2) {
     double sw = 0, s1[kMaxRes], s2[kMaxRes];
     for (int r = 0; r < NR; ++r) s1[r] = s2[r] = 0;
     // thread q < NRE + NIM owns sum entry q: Re S_jk over j <= k, then Im S_jk over j < k (row-major)
@@ -334,9 +340,13 @@ __global__ void __launch_bounds__(kGT, 1) k_generic_tiles(const __grid_constant_
     __syncthreads();
   }
 
-  // ---- data tiles: ln B of Eq. (mix) and its adjoint
-  {
-    double lnb = 0, gx = 0, gy = 0, nbad = 0;
+  // ---- data tiles: ln B of Eq. (mix) and its adjoint (with a background:
+  // ln of the mixture density and the adjoint weighted by the signal share)
+  if (PASS != 1) {
+    double lnb = 0, gx = 0, gy = 0, nbad = 0, sum_ws = 0;
+    const double* part_in = static_cast<const double*>(a.part);
+    const double Nsig = PASS == 2 ? part_in[size_t(G) * wd.W] : 0.0;  // N from k_generic_norm
+    const double fb = a.km.bkg_fraction, taub = a.km.bkg_tau;
     int lexp = 0;
     double gAr[kMaxComp], gAi[kMaxComp], gBr[kMaxComp], gBi[kMaxComp], s1[kMaxRes], s2[kMaxRes];
     const double2* logtab = static_cast<const double2*>(a.logtab);
@@ -353,13 +363,53 @@ __global__ void __launch_bounds__(kGT, 1) k_generic_tiles(const __grid_constant_
       double Ar, Ai, Br, Bi, tAr, tAi, tBr, tBi;
       ev.amplitudes(g, Ar, Ai, Br, Bi);
       const double t_e = pl[npl * kGT];
-      const bool ok = mix_event<PrecF64, GRAD>(g.bc, logtab, Ar, Ai, Br, Bi, Ar, Ai, Br, Bi, t_e, lnb, lexp,
-                                               a.rates ? a.rates + i : nullptr, tAr, tAi, tBr, tBi, gx, gy);
+      bool ok;
+      double R = 0, gxe = 0, gye = 0;  // the event's rate and its d ln R / dx, d ln R / dy
+      if (a.km.sigma_t > 0) {  // Eq. (mix) folded with the decay-time resolution: ln R, R with e^{-Gamma t}
+        ok = resolved_rate<GRAD>(Ar, Ai, Br, Bi, t_e, g.bc.x, g.bc.y, g.bc.gamma, a.km.sigma_t, R, tAr, tAi, tBr,
+                                 tBi, gxe, gye);
+        if (ok && PASS == 0) lnb += log(R);
+      } else {
+        double lnb_e = 0;
+        int lexp_e = 0;
+        ok = mix_event<PrecF64, GRAD>(g.bc, logtab, Ar, Ai, Br, Bi, Ar, Ai, Br, Bi, t_e, lnb_e, lexp_e, &R, tAr, tAi,
+                                      tBr, tBi, gxe, gye);
+        if (ok && PASS == 0) {
+          lnb += lnb_e;
+          lexp += lexp_e;
+        }
+      }
+      if (a.rates) a.rates[i] = R;
+      double ws = 1.0;  // weight of the signal sensitivities: 1, or the signal share of the mixture
+      if (PASS == 2 && ok) {
+        // background density: e^{-t/tau_b} / tau_b in the true time, folded with the resolution if any
+        double Bb;
+        if (a.km.sigma_t > 0) {
+          Cplx K, dK;
+          fold_exp(t_e, Cplx{1.0 / taub, 0.0}, a.km.sigma_t, K, dK);
+          Bb = K.re / taub;
+        } else {
+          Bb = t_e >= 0 ? exp(-t_e / taub) / taub : 0.0;
+        }
+        const double Ls = (1.0 - fb) * R / Nsig, L = Ls + fb * Bb;
+        ok = L > 0 && L < INFINITY;
+        if (ok) {
+          lnb += log(L);
+          ws = Ls / L;
+          sum_ws += ws;
+        }
+      }
       if (!ok) {
         nbad += 1;
         continue;
       }
       if (GRAD) {
+        gx += ws * gxe;
+        gy += ws * gye;
+        tAr *= ws;
+        tAi *= ws;
+        tBr *= ws;
+        tBi *= ws;
         for (int j = 0; j < U; ++j) {
           cmac(gAr[j], gAi[j], tAr, tAi, ev.ar[j], ev.ai[j]);
           cmac(gBr[j], gBi[j], tBr, tBi, ev.ar[j], ev.ai[j]);
@@ -382,11 +432,21 @@ __global__ void __launch_bounds__(kGT, 1) k_generic_tiles(const __grid_constant_
           return c < NR ? s1[c] : s2[c - NR];
         },
         red, row + wd.WMC);
-    if (tid == 0) row[wd.W - 1] = 0.0;
-    __syncthreads();
+    // the last data column: 0, or with a background the sum of the signal shares
+    {
+      const double v = warp_sum(sum_ws);
+      if ((tid & 31) == 0) red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double sws = 0;
+        for (int w = 0; w < kGW; ++w) sws += red[w];
+        row[wd.W - 1] = PASS == 2 ? sws : 0.0;
+      }
+      __syncthreads();
+    }
   }
   double* part = static_cast<double*>(a.part);
-  for (int c = tid; c < wd.W; c += kGT) part[b * wd.W + c] = row[c];
+  for (int c = PASS == 2 ? wd.WMC + tid : tid; c < (PASS == 1 ? wd.WMC : wd.W); c += kGT) part[b * wd.W + c] = row[c];
 }
 
 // Sums the partial rows of G blocks in block order and writes the result
@@ -395,7 +455,12 @@ __global__ void __launch_bounds__(kGT, 1) k_generic_tiles(const __grid_constant_
 // gram_store.  The formulas are those of finish_likelihood:
 //   N = tau <alpha |A|^2 + beta |Abar|^2 - 2 gc Re(A Abar*) - 2 dc Im(A Abar*)>
 //   NLL = -sum ln B + Gamma sum t + N_data ln N.
-__global__ void __launch_bounds__(kGT) k_generic_finish(const __grid_constant__ EvalArgs a, int G, int want_grad) {
+// mode 0: the result; mode 1 (background, between the MC and the data
+// pass): only N, into part[G * W]; mode 2 (background, last): the result of
+// the mixture, NLL = -sum ln((1 - f) R/N + f B), its normalisation term
+// weighted by the sum of the events' signal shares instead of N_data.
+__global__ void __launch_bounds__(kGT) k_generic_finish(const __grid_constant__ EvalArgs a, int G, int want_grad,
+                                                        int mode) {
   __shared__ double col[kMaxW];
   __shared__ CtaConst cc;  // d ln kappa / d m0, d ln kappa / d Gamma0 (kappa_log_derivatives)
   const int tid = threadIdx.x;
@@ -415,7 +480,8 @@ __global__ void __launch_bounds__(kGT) k_generic_finish(const __grid_constant__ 
     if (m0 > 0 && g0 > 0) kappa_log_derivatives(km, tid, m0, g0, cc);
   }
   __syncthreads();
-  for (int c = tid; c < wd.WMC; c += kGT) a.gram_store[c] = col[c];
+  if (mode != 1)
+    for (int c = tid; c < wd.WMC; c += kGT) a.gram_store[c] = col[c];
   if (tid != 0) return;
   auto put = [&](int k, double v) {
     a.result[k] = v;
@@ -437,9 +503,14 @@ __global__ void __launch_bounds__(kGT) k_generic_finish(const __grid_constant__ 
       }
     }
     if (!(fabs(par(np - 1)) < 1.0)) status = -6;
+    if (km.sigma_t > 0 && !(fabs(par(np - 2)) * km.gamma * km.sigma_t * 0.70710678118654752 <= kMaxResolutionMix))
+      status = -6;
   }
+  double* n_out = const_cast<double*>(part) + size_t(G) * wd.W;  // N for the data pass of a background
   if (status != 0) {
-    for (int k = 0; k < kResHeader + np; ++k) put(k, k == 2 ? double(status) : nan(""));
+    if (mode == 1) *n_out = nan("");
+    else
+      for (int k = 0; k < kResHeader + np; ++k) put(k, k == 2 ? double(status) : nan(""));
     return;
   }
   double cA[kMaxComp][2] = {}, cB[kMaxComp][2] = {};
@@ -480,9 +551,16 @@ __global__ void __launch_bounds__(kGT) k_generic_finish(const __grid_constant__ 
   const double inv_sw = a.inv_sum_w;
   const double nbar = (al * AA + be * BB - 2.0 * gc * Xr - 2.0 * dc * Xi) * inv_sw;
   const double N = nbar * km.tau;
+  if (mode == 1) {
+    *n_out = N;
+    return;
+  }
   const double* ds = col + wd.WMC;
-  const double Nd = double(a.data.n);
-  double nll = -ds[0] + gamma * a.sum_t + Nd * log(N);
+  // the weight of d ln N: the number of data events, or with a background the sum of their signal shares
+  const double Nd = mode == 2 ? ds[wd.WD - 1] : double(a.data.n);
+  // sum ln B leaves out e^{-Gamma t}; the folded rates of a decay-time resolution include it; with a
+  // background the data pass summed ln of the whole normalised density
+  double nll = mode == 2 ? -ds[0] : -ds[0] + (km.sigma_t > 0 ? 0.0 : gamma * a.sum_t) + Nd * log(N);
   if (ds[1] > 0 || !(N > 0)) nll = nan("");
   put(0, nll);
   put(1, N);
@@ -534,10 +612,18 @@ __global__ void __launch_bounds__(kGT) k_generic_finish(const __grid_constant__ 
 int g_generic_smem_set[64] = {};
 std::mutex g_generic_mu;
 
-template <bool GRAD>
+template <bool GRAD, int PASS>
 cudaError_t launch_tiles(int grid, int smem, cudaStream_t st, const EvalArgs& a) {
-  k_generic_tiles<GRAD><<<grid, kGT, smem, st>>>(a);
+  k_generic_tiles<GRAD, PASS><<<grid, kGT, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int PASS>
+cudaError_t allow_tiles_smem(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_generic_tiles<true, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_generic_tiles<false, PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
 }
 
 }  // namespace
@@ -553,15 +639,24 @@ cudaError_t generic_eval(bool /*full*/, bool grad, int grid, bool /*pdl*/, cudaS
   {
     std::lock_guard<std::mutex> lk(g_generic_mu);
     if (dev >= 0 && dev < 64 && !g_generic_smem_set[dev]) {
-      if ((e = cudaFuncSetAttribute(k_generic_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) ||
-          (e = cudaFuncSetAttribute(k_generic_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+      if ((e = allow_tiles_smem<0>(smem)) || (e = allow_tiles_smem<1>(smem)) || (e = allow_tiles_smem<2>(smem)))
         return e;
       g_generic_smem_set[dev] = 1;
     }
   }
-  e = grad ? launch_tiles<true>(grid, smem, st, a) : launch_tiles<false>(grid, smem, st, a);
+  if (a.km.bkg_fraction > 0) {  // MC pass, N, data pass with the mixture, result
+    e = grad ? launch_tiles<true, 1>(grid, smem, st, a) : launch_tiles<false, 1>(grid, smem, st, a);
+    if (e != cudaSuccess) return e;
+    k_generic_finish<<<1, kGT, 0, st>>>(a, grid, 0, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = grad ? launch_tiles<true, 2>(grid, smem, st, a) : launch_tiles<false, 2>(grid, smem, st, a);
+    if (e != cudaSuccess) return e;
+    k_generic_finish<<<1, kGT, 0, st>>>(a, grid, grad ? 1 : 0, 2);
+    return cudaGetLastError();
+  }
+  e = grad ? launch_tiles<true, 0>(grid, smem, st, a) : launch_tiles<false, 0>(grid, smem, st, a);
   if (e != cudaSuccess) return e;
-  k_generic_finish<<<1, kGT, 0, st>>>(a, grid, grad ? 1 : 0);
+  k_generic_finish<<<1, kGT, 0, st>>>(a, grid, grad ? 1 : 0, 0);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ struct ShapeOps {
   // (EvalArgs::derived); null where the path derives them itself
   cudaError_t (*derive)(int K, const double* params, int np, const ModelConst& km, void* out, cudaStream_t st);
   int64_t derived_bytes;
+  int cached_blocks;  // blocks per SM of the cached pass (component cache in, no MC tiles)
 };
 
 // Launcher of the runtime-table evaluation (generic.cu) for model

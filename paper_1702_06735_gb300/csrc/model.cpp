@@ -58,6 +58,17 @@ CompiledModel compile_model(const std::string& text) {
   m.y = d.at("y").number();
   m.float_xy = get_bool(d, "float_xy", true);
   m.dedup = get_bool(d, "dedup", true);
+  if (const Json* r = d.find("time_resolution"); r && r->kind != Json::Null) {
+    m.sigma_t = r->number();
+    if (!(m.sigma_t >= 0) || !std::isfinite(m.sigma_t))
+      throw std::runtime_error("model: time_resolution must be a width >= 0 (ps)");
+  }
+  if (const Json* bg = d.find("background"); bg && bg->kind != Json::Null) {
+    m.bkg_fraction = bg->at("fraction").number();
+    m.bkg_tau = bg->at("tau").number();
+    if (!(m.bkg_fraction >= 0 && m.bkg_fraction < 1) || !(m.bkg_tau > 0) || !std::isfinite(m.bkg_tau))
+      throw std::runtime_error("model: background needs 0 <= fraction < 1 and tau > 0 (ps)");
+  }
 
   for (const Json& r : d.at("resonances").array()) {
     ResonanceDef rd;

@@ -75,6 +75,13 @@ struct CompiledModel {
   int bose[2] = {-1, -1};
   double x = 0, y = 0;
   bool float_xy = true;
+  // Gaussian decay-time resolution (ps); 0: none.  An extension the paper
+  // leaves out (Sec. 4); evaluated by the runtime-table kernels.
+  double sigma_t = 0;
+  // Background (an extension the paper leaves out, Sec. 4): a fraction of
+  // the data events flat in phase space with an exponential decay time of
+  // lifetime bkg_tau; evaluated by the runtime-table kernels.
+  double bkg_fraction = 0, bkg_tau = 1;
   bool dedup = true;
   std::vector<ResonanceDef> res;
   std::vector<ChainDef> chains;

@@ -89,6 +89,105 @@ def run(model, precision: str, sizes, gen_params, mc, seed: int, stream0: int = 
         srv.close()
 
 
+@dataclass
+class FloatingFit:
+    n_events: int
+    params: np.ndarray
+    errors: np.ndarray
+    converged: bool
+    n_eval: int
+    xy_fixed_model: tuple = ()  # (x, y, sx, sy) of the fixed-model fit of the same events, if asked for
+
+
+def run_floating(model, precision: str, sizes, gen_params, mc, seed: int, stream0: int = 1000, floating=None,
+                 start_shift: float = 1e-3, scale=None, compare_fixed: bool = False):
+    """Pseudo-experiments fitted with the model floating: every parameter of
+    the `floating` mask (default: every resonance mass and width with x and
+    y; the chain coefficients stay at their generating values, since a
+    floating DCS phase is nearly degenerate with x and y in the 2-chain
+    model, whose strong phase varies little over phase space), an extension
+    of the paper's fixed-model study (Sec. 4).  A floating
+    model has no fixed component cache, so the fits run on one likelihood
+    context (full evaluations, MC sums recomputed each time) instead of the
+    serving loop; each toy is generated on the device with the same
+    (seed, stream) as run() uses, so both studies fit the same events.
+    Errors from the Hessian over all floating parameters.  With
+    compare_fixed, the same events are also fitted with the model fixed (x, y
+    floating), whose errors are the conditional ones.  Returns a list of
+    FloatingFit."""
+    from .tdmix import TDMix
+    gen_params = np.asarray(gen_params, dtype=np.float64)
+    c = TDMix(model, precision)
+    try:
+        if floating is None:
+            mask = _model_mask(model)
+            mask[:2 * len(_model_dict(model)["chains"])] = False
+        else:
+            mask = np.asarray(floating, dtype=bool)
+        c.set_floating(mask.astype(np.int32))
+        n_chains = sum(1 for _ in _model_dict(model)["chains"])
+        n_res = len(_model_dict(model)["resonances"])
+        sc = minimize.default_scales(gen_params, n_chains, n_res) if scale is None else scale
+        fg = minimize.safe_objective(c)
+        c.load_events(mc_p4=mc)
+        out = []
+        env = 0.0  # the generator's envelope, found by the first toy and reused (same parameters)
+        for k, n in enumerate(sizes):
+            p4, t, info = c.generate(int(n), seed=seed, stream=stream0 + k, params=gen_params, envelope=env)
+            env = info["envelope"]
+            c.load_events(p4, t)
+            g = np.random.default_rng(seed + 7919 * k)
+            x0 = gen_params.copy()
+            x0[mask] += start_shift * sc[mask] * g.uniform(-1, 1, int(mask.sum()))
+            r = minimize.bfgs(fg, x0, floating=mask, scale=sc, gtol=1e-3, edm_tol=1e-6, max_iter=400)
+            err = minimize.errors(fg, r.x, mask) if r.converged else np.full(len(r.x), np.nan)
+            fit = FloatingFit(int(n), r.x.copy(), err, bool(r.converged), int(r.n_eval) + 2 * int(mask.sum()))
+            if compare_fixed:
+                mxy = np.zeros(len(mask), dtype=bool)
+                mxy[-2:] = True
+                q0 = gen_params.copy()
+                q0[-2:] = x0[-2:]
+                c.set_floating(mxy.astype(np.int32))
+                rf = minimize.bfgs(fg, q0, floating=mxy, scale=sc, gtol=1e-3, edm_tol=1e-6, max_iter=100)
+                ef = minimize.errors(fg, rf.x, mxy) if rf.converged else np.full(len(rf.x), np.nan)
+                fit.xy_fixed_model = (float(rf.x[-2]), float(rf.x[-1]), float(ef[-2]), float(ef[-1]))
+                c.set_floating(mask.astype(np.int32))
+            out.append(fit)
+        return out
+    finally:
+        c.close()
+
+
+def _model_dict(model) -> dict:
+    import json
+    from .tdmix import model_json
+    return json.loads(model_json(model))
+
+
+def _model_mask(model) -> np.ndarray:
+    """The model file's floating mask (parameter order of the library)."""
+    d = _model_dict(model)
+    m = []
+    for ch in d["chains"]:
+        m += [ch.get("float", True)] * 2
+    for r in d["resonances"]:
+        m += [r.get("float", True)] * 2
+    m += [d.get("float_xy", True)] * 2
+    return np.asarray(m, dtype=bool)
+
+
+def floating_pulls(fits, truth, index) -> dict:
+    """Resolution and pulls of parameter `index` over converged fits."""
+    ok = [f for f in fits if f.converged and np.isfinite(f.errors[index]) and f.errors[index] > 0]
+    v = np.asarray([f.params[index] for f in ok])
+    e = np.asarray([f.errors[index] for f in ok])
+    pu = (v - truth[index]) / e
+    n = len(pu)
+    return {"used": n, "sigma": float(v.std(ddof=1)), "mean_error": float(e.mean()),
+            "pull_mean": float(pu.mean()), "pull_mean_err": float(pu.std(ddof=1) / math.sqrt(n)),
+            "pull_width": float(pu.std(ddof=1)), "pull_width_err": float(pu.std(ddof=1) / math.sqrt(2 * (n - 1)))}
+
+
 def pulls(fits, x_true: float, y_true: float) -> dict:
     """Resolution and pull summary of converged toy fits with errors:
     sigma = standard deviation of the fitted values, the mean fitted error,
