@@ -194,9 +194,15 @@ def blatt_weisskopf(L: int, q2, r: float):
 
 
 def mass_dependent_width(s, m0, g0, L: int, ma: float, mb: float, r: float):
+    """Gamma(s) = Gamma0 (m0/sqrt s) (q/q0)^(2L+1) [F_L(q r)/F_L(q0 r)]^2, and 0
+    below the threshold of the nominal daughters (q = 0 there; the square
+    root is taken only where q^2 > 0, so that the derivative in m0 is 0
+    there rather than 0 times an infinite one)."""
     q2 = breakup_q2(s, ma * ma, mb * mb)
     q02 = breakup_q2(m0 * m0, ma * ma, mb * mb)
-    ratio = torch.sqrt(q2 / q02) ** (2 * L + 1)
+    above = q2 > 0
+    q2s = torch.where(above, q2, torch.ones_like(q2))
+    ratio = torch.where(above, torch.sqrt(q2s / q02) ** (2 * L + 1), torch.zeros_like(q2))
     ff = (blatt_weisskopf(L, q2, r) / blatt_weisskopf(L, q02, r)) ** 2
     return g0 * (m0 / torch.sqrt(s)) * ratio * ff
 

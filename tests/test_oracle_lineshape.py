@@ -174,3 +174,28 @@ def test_mdw_width_values_k_star():
         got = float(tdamp.mass_dependent_width(torch.tensor(rs * rs, dtype=F64), torch.tensor(m0, dtype=F64),
                                                torch.tensor(g0, dtype=F64), 1, M_K, M_PI, 1.5))
         assert abs(got / want - 1) < 5e-6, (rs, got, want)
+
+
+def test_mdw_width_vanishes_below_threshold_with_finite_gradient():
+    """A quasi-two-body state given a mass-dependent width to its sub-resonance
+    at the nominal mass and the bachelor (the a1 to rho0 pi-): below that
+    threshold Gamma(s) = 0, so BW = 1/(m0^2 - s), and the derivatives in m0
+    and Gamma0 are those of that real lineshape (finite), not NaN."""
+    import torch
+    from oracle import tdamp
+    res = tdamp.Resonance("a1", 1.23, 0.42, "MDW", 0, (0.77526, 0.13957), True)
+    s = torch.tensor([0.5, 0.8, 1.2, 1.6], dtype=torch.float64)   # the first two below (0.915 GeV)^2
+    m0 = torch.tensor(1.23, dtype=torch.float64, requires_grad=True)
+    g0 = torch.tensor(0.42, dtype=torch.float64, requires_grad=True)
+    bw = tdamp.breit_wigner(s, m0, g0, res, 1.5)
+    below = s < (0.77526 + 0.13957) ** 2
+    assert torch.equal(bw[below], (1.0 / (m0 * m0 - s[below])).to(torch.complex128))
+    dm, dg = torch.autograd.grad(bw.real.sum() + bw.imag.sum(), (m0, g0))
+    assert torch.isfinite(dm) and torch.isfinite(dg)
+    # below threshold d(1/(m0^2 - s))/dm0 = -2 m0 / (m0^2 - s)^2, and nothing depends on Gamma0
+    m0_, s_ = 1.23, s[below]
+    ref = float((-2 * m0_ / (m0_ ** 2 - s_) ** 2).sum())
+    above = s[~below]
+    dm_above = torch.autograd.grad((tdamp.breit_wigner(above, m0, g0, res, 1.5).real.sum()
+                                    + tdamp.breit_wigner(above, m0, g0, res, 1.5).imag.sum()), m0)[0]
+    assert abs(float(dm) - (ref + float(dm_above))) <= 1e-12 * abs(float(dm))
