@@ -130,10 +130,13 @@ def kernel_source_digest():
 
 
 # DRAM bytes read + written by one launch of the headline evaluation kernel
-# (k_eval, fp32 path, all parameters moved), from one ncu capture of this
-# command with warm caches; valid only for the kernel sources of the digest
-# below (the figure is reported as null once the sources change)
-TRAFFIC = {"bytes_per_launch": None, "sources_sha256": None}
+# (k_eval, fp32 path, all parameters moved), from one ncu capture with warm
+# caches (the second of two captured launches of `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum --cache-control none -k
+# regex:k_eval -s 5 -c 2 python bench.py --studies none --steps 5 --warmup 3
+# --no-cpu-baseline`); valid only for the kernel sources of the digest below
+# (the figure is reported as null once the sources change)
+TRAFFIC = {"bytes_per_launch": 141739008 + 3721728, "sources_sha256": "35402852a2bdb914d10efa71d599c71885c49d0646c773f3c35c88722d8d859e"}
 
 
 def step_params(p0, move, k: int):
@@ -163,7 +166,7 @@ def class_masks(n_params, nc, nr):
 # clocks during the timed region
 # ----------------------------------------------------------------------------
 class ClockSampler:
-    """SM clock and clock-event reasons polled every 2 ms through NVML's
+    """SM clock and clock-event reasons polled every 0.2 ms through NVML's
     read-only queries while the timed region runs (nvidia-smi at 200 ms
     where NVML is not available)."""
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
@@ -208,7 +211,7 @@ class ClockSampler:
             if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) == 0 and \
                     self.reasons_fn(self.h, ctypes.byref(r)) == 0:
                 self.samples.append((time.perf_counter(), float(c.value), int(r.value)))
-            time.sleep(0.002)
+            time.sleep(0.0002)
 
     def _read_smi(self):
         for line in self.smi.stdout:
@@ -262,7 +265,7 @@ class ClockSampler:
         reasons = sorted({name for _, _, m in used for bit, name in self.REASONS.items() if m & bit})
         return {"sm_mhz": statistics.median(s[1] for s in used), "sm_max_mhz": self.max_mhz, "reasons": reasons,
                 "samples": len(used), "in_timed_region": len(inside),
-                "source": "NVML, 2 ms polling" if self.lib is not None else "nvidia-smi, 200 ms"}
+                "source": "NVML, 0.2 ms polling" if self.lib is not None else "nvidia-smi, 200 ms"}
 
 
 def measured_peaks():

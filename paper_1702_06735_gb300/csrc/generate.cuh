@@ -64,10 +64,6 @@ struct GenArgs {
   int64_t ld, out_end;       // plane stride; positions >= out_end are not written
 };
 
-// Float in [0, 1) from the top 23 bits of a: exact (the bit pattern of
-// 1 + k 2^-23 minus 1), and u01(a, b) - u01f(a) lies in [0, 2^-22).
-__device__ __forceinline__ float u01f(uint32_t a) { return __uint_as_float(0x3F800000u | (a >> 9)) - 1.0f; }
-
 // The random draws of one candidate: draw word d of its counter gives two
 // doubles in [0, 1) (d = 0: decay time and acceptance; d = 1: the Gaussian
 // of a decay-time resolution; d = 8 + 5 try + j: GENBOD try `try`).
@@ -77,16 +73,7 @@ struct CandRng {
     const Philox4 r = philox4x32_10(Philox4{{c0, c1, stream, d}}, k0, k1);
     return make_double2(u01(r.v[0], r.v[1]), u01(r.v[2], r.v[3]));
   }
-  // The same two uniforms truncated to floats: each is below its double by
-  // less than 2^-22 (u01f), so single-precision decisions can bound them.
-  __device__ float2 pairf(uint32_t d) const {
-    const Philox4 r = philox4x32_10(Philox4{{c0, c1, stream, d}}, k0, k1);
-    return make_float2(u01f(r.v[0]), u01f(r.v[2]));
-  }
 };
-
-constexpr float kGapMin = 1.0f / 1024;  // smallest mass gap decided in single precision
-constexpr float kUErr = 2.384185791e-7f;  // 2^-22: bound of u01 - u01f
 
 template <class T>
 __device__ __forceinline__ T breakup(T M, T a, T b) {
@@ -125,36 +112,39 @@ __device__ __forceinline__ float breakup_gap(float M, float a, float b, float ga
   return sqrtf(fmaxf(l, 0.f)) / (2.f * M);
 }
 
-// The first accepted GENBOD try of a candidate (-1 if all kGenMaxTries
-// fail), decided in single precision wherever that provably agrees with
-// double precision, else on the double-precision weight and uniform:
-//   * the uniforms as truncated floats (each below its double by less than
-//     2^-22, u01f);
-//   * the three mass gaps ra, rb - ra, 1 - rb (in units of the kinetic
-//     energy) at least 2^-10, so their relative errors stay below 2^-12 and
-//     the three breakup momenta, formed from the factored Kallen function,
-//     within about 1.2e-4 each (3.6e-4 for the product);
-//   * accepted if u + 2^-22 < w (1 - 1e-3), rejected if u >= w (1 + 1e-3);
-//     otherwise (or with a smaller gap) decided in double precision.
-// So the try found is the one double precision finds.
-__device__ inline int genbod_try(const GenArgs& a, const CandRng& rng) {
+// The GENBOD weight of try `tr` in single precision: the three mass gaps
+// ra, rb - ra, 1 - rb (in units of the kinetic energy) are taken in double
+// precision and rounded once, and each breakup momentum comes from the
+// factored Kallen function, so the weight is within a few float roundings
+// (about 1e-6 relative) of its double-precision value even next to a
+// threshold, where M^2 - (a + b)^2 would cancel.
+__device__ __forceinline__ float genbod_weight_f(const GenArgs& a, const CandRng& rng, int tr, double& u_acc) {
+  const uint32_t d0 = 8u + 5u * uint32_t(tr);
+  const double2 u0 = rng.pair(d0), u1 = rng.pair(d0 + 1);
+  u_acc = u1.x;
+  const double rad = fmin(u0.x, u0.y), rbd = fmax(u0.x, u0.y);
+  const float te = float(a.tecm);
+  const float g1 = float(rad) * te, g2 = float(rbd - rad) * te, g3 = float(1.0 - rbd) * te;
   const float m0 = float(a.m[0]), m1 = float(a.m[1]), m2 = float(a.m[2]), m3 = float(a.m[3]);
-  const float te = float(a.tecm), mD = float(a.mD), iw = float(a.inv_wtmax);
+  const float M1 = m0 + m1 + float(rad) * te, M2 = m0 + m1 + m2 + float(rbd) * te;
+  return breakup_gap(M1, m0, m1, g1) * breakup_gap(M2, M1, m2, g2) * breakup_gap(float(a.mD), M2, m3, g3) *
+         float(a.inv_wtmax);
+}
+
+// The first accepted GENBOD try of a candidate (-1 if all kGenMaxTries
+// fail).  Each try's weight is formed in single precision (genbod_weight_f)
+// with a band of 1e-5 of it (about ten times its rounding error); a try
+// whose uniform falls inside the band is decided on the double-precision
+// weight, so the try found is the one double precision finds.
+__device__ inline int genbod_try(const GenArgs& a, const CandRng& rng) {
   for (int tr = 0; tr < kGenMaxTries; ++tr) {
-    const uint32_t d0 = 8u + 5u * uint32_t(tr);
-    const float2 u0 = rng.pairf(d0), u1 = rng.pairf(d0 + 1);
-    const float ra = fminf(u0.x, u0.y), rb = fmaxf(u0.x, u0.y);
-    const float g1 = ra, g2 = rb - ra, g3 = 1.0f - rb;
-    if (fminf(g1, fminf(g2, g3)) >= kGapMin) {
-      const float M1 = m0 + m1 + ra * te, M2 = m0 + m1 + m2 + rb * te;
-      const float w = breakup_gap(M1, m0, m1, g1 * te) * breakup_gap(M2, M1, m2, g2 * te) *
-                      breakup_gap(mD, M2, m3, g3 * te) * iw;
-      if (u1.x + kUErr < w * (1.0f - 1e-3f)) return tr;
-      if (u1.x >= w * (1.0f + 1e-3f)) continue;
-    }
-    double u_acc;
-    const double w64 = genbod_weight<double>(a, rng, tr, u_acc);
-    if (u_acc < w64) return tr;
+    double u;
+    const float w = genbod_weight_f(a, rng, tr, u);
+    const double lo = double(w) * (1.0 - 1e-5), hi = double(w) * (1.0 + 1e-5);
+    if (u < lo) return tr;
+    if (u >= hi) continue;
+    double u64;
+    if (u < genbod_weight<double>(a, rng, tr, u64)) return tr;
   }
   return -1;
 }
@@ -272,7 +262,7 @@ struct RegSrcF {
 // the magnitude the rounding errors of Z scale with (see ill_conditioned).
 template <class S>
 __device__ inline void event_weight_f32(const DevModel* __restrict__ dm, const BlockConst<float>& bc,
-                                        const V4T<float> (&q)[4], float t, float& w, float& band) {
+                                        const V4T<float> (&q)[4], double t, float& w, float& band) {
   constexpr int NS = S::NS > 0 ? S::NS : 1, NX = S::NX > 0 ? S::NX : 1, NT = S::U * S::NO;
   float sv[NS], xv[NX], kv[NT];
 #pragma unroll
@@ -315,7 +305,7 @@ __device__ inline void event_weight_f32(const DevModel* __restrict__ dm, const B
     SA = fmaf(fabsf(C.x) + fabsf(C.y), sc[j], SA);
     SB = fmaf(fabsf(C.z) + fabsf(C.w), sc[j], SB);
   }
-  const float tg = bc.gammaf * t;
+  const float tg = bc.gammaf * float(t);
   const float a = 0.5f * bc.yf * tg, b = 0.5f * bc.xf * tg;
   float cha, sha, cb, sb, chw, shw, c0, s0;
   mixing_trig_f32(a, b, cha, sha, cb, sb);
@@ -327,13 +317,7 @@ __device__ inline void event_weight_f32(const DevModel* __restrict__ dm, const B
   const float f = 2.0f * expf(-fabsf(bc.yf) * tg);
   const float z2 = Zr * Zr + Zi * Zi;
   w = f * z2;
-  // The time t carries a relative error below 2^-13 (k_gen_pass1).  With
-  // dZ/dt = (y + i x) Gamma/2 (sinh(w) A - cosh(w) Abar), |d|Z|^2/dt| <=
-  // (|x| + |y|) Gamma S_Z cosh|w| (S_A + S_B) and d e^{-|y| Gamma t}/dt adds
-  // |y| Gamma of the weight; twice their sum times 2^-13 t covers the time's error.
-  const float dt = 1.220703125e-4f * tg;  // 2^-13 Gamma t
-  const float tband = 2.0f * dt * ((fabsf(bc.xf) + fabsf(bc.yf)) * SZ * chw * (SA + SB) + fabsf(bc.yf) * z2);
-  band = f * (1e-3f * z2 + 1e-4f * SZ * SZ + tband);
+  band = f * (1e-3f * z2 + 1e-4f * SZ * SZ);
 }
 
 template <class S>
@@ -372,38 +356,29 @@ __global__ void __launch_bounds__(kGenThreads) k_gen_pass1(const __grid_constant
     bool acc = tr >= 0;
     if (acc && !a.flat) {
       const double2 u = rng.pair(0);
+      const double t = -log1p(-u.x) / a.lambda;
+      const double thr = u.y * a.env;
       bool decided = false;
-      // single precision, for decay times below ~7 lifetimes (1 - u >= 2^-10): the uniforms
-      // rounded to floats (relative 2^-24), t = -log1p(-u) / lambda in floats (relative error
-      // below 2^-13: 2^-24 / (1 - u) from u, a few ulps from log1pf), thr = u env; the
-      // band of event_weight_f32 covers the rate's and the time's errors, and the
-      // comparisons keep a relative margin of 1e-6 for the float roundings
-      const float ut = float(u.x);
-      if (a.prescreen && ut <= 1.0f - kGapMin) {
-        const float tf = -log1pf(-ut) / float(a.lambda);
+      if (a.prescreen) {
         V4T<float> pf[4];
         genbod_momenta<float>(a, rng, tr, pf);
         float w32, band;
-        event_weight_f32<S>(a.dm, bf, pf, tf, w32, band);
-        const float hi = (w32 + band) * (1.0f + 1e-6f), lo = (w32 - band) * (1.0f - 1e-6f);
-        const float envf = float(a.env) * (1.0f - 1e-6f);
-        const float thr = float(u.y) * float(a.env);
+        event_weight_f32<S>(a.dm, bf, pf, t, w32, band);
+        const double hi = double(w32) + double(band);
         // decided in single precision unless u env lies in the band, or the
         // weight could exceed the envelope (the violation check uses exact
         // weights; the pilot, which sets the envelope, runs without the
         // pre-screen)
-        if (hi <= envf) {
-          if (thr * (1.0f + 1e-6f) < lo) {
+        if (hi <= a.env) {
+          if (thr < double(w32) - double(band)) {
             acc = decided = true;
-          } else if (thr * (1.0f - 1e-6f) > hi) {
+          } else if (thr > hi) {
             acc = false;
             decided = true;
           }
         }
       }
       if (!decided) {
-        const double t = -log1p(-u.x) / a.lambda;
-        const double thr = u.y * a.env;
         V4 p[4];
         genbod_momenta<double>(a, rng, tr, p);
         const double w = event_rate<S>(a.dm, bc, p, t) * exp(a.lambda * t);
