@@ -136,7 +136,9 @@ int tdmix_create(const char* model_json, int precision, tdmix_ctx** out);
 int tdmix_kernel_path(const tdmix_ctx* ctx);
 
 /* Uses the given cudaStream_t (NULL: the legacy default stream) for all
- * later work of the context. */
+ * later work of the context.  Work already enqueued on the previous stream
+ * is waited for first (the context's buffers are then reused on the new
+ * one). */
 int tdmix_set_stream(tdmix_ctx* ctx, void* cuda_stream);
 
 /* Length of the parameter vector, or a negative status. */

@@ -637,11 +637,13 @@ cudaError_t generic_eval(bool /*full*/, bool grad, int grid, bool /*pdl*/, cudaS
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   {
+    // the attribute acts per device: set once per device (every time beyond the table's devices)
     std::lock_guard<std::mutex> lk(g_generic_mu);
-    if (dev >= 0 && dev < 64 && !g_generic_smem_set[dev]) {
+    const bool known = dev >= 0 && dev < 64;
+    if (!known || !g_generic_smem_set[dev]) {
       if ((e = allow_tiles_smem<0>(smem)) || (e = allow_tiles_smem<1>(smem)) || (e = allow_tiles_smem<2>(smem)))
         return e;
-      g_generic_smem_set[dev] = 1;
+      if (known) g_generic_smem_set[dev] = 1;
     }
   }
   if (a.km.bkg_fraction > 0) {  // MC pass, N, data pass with the mixture, result
