@@ -267,6 +267,90 @@ struct EventCore {
     }
   }
 
+  // components() that also keeps every term's product Q_t = K_t prod BW
+  // (the term's contribution to its component) for backprop_q.
+  template <class Src>
+  __device__ __forceinline__ void components_q(const Src& src, T (&qr)[U * NO], T (&qi)[U * NO]) {
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      T sr = 0, si = 0;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        const int t = j * NO + o;
+        const int b0 = S::tb0(t), b1 = S::tb1(t);
+        const T K = src.k(t);
+        T pr, pi;
+        if (b0 >= 0 && b1 >= 0) {
+          pr = fma(bwr[b0], bwr[b1], -bwi[b0] * bwi[b1]);
+          pi = fma(bwr[b0], bwi[b1], bwi[b0] * bwr[b1]);
+        } else if (b0 >= 0) {
+          pr = bwr[b0]; pi = bwi[b0];
+        } else if (b1 >= 0) {
+          pr = bwr[b1]; pi = bwi[b1];
+        } else {
+          pr = 1; pi = 0;
+        }
+        qr[t] = K * pr;
+        qi[t] = K * pi;
+        sr += qr[t];
+        si += qi[t];
+      }
+      ar[j] = sr;
+      ai[j] = si;
+    }
+  }
+
+  // backprop_lineshapes from the kept term products: with W_j = gA cA_j +
+  // gB cB_j, df/dBW_b = Z_b / BW_b, Z_b = sum over the terms t of b of
+  // W_j(t) Q_t (a term holding b twice counts twice), so H_b = (df/dBW_b)
+  // BW_b^2 = Z_b BW_b.  The same sums as backprop_lineshapes with fewer
+  // operations: no K reloads, no BW_b^2.
+  template <bool WEIGHTED>
+  __device__ __forceinline__ void backprop_q(const BlockConst<T>& bc, const T (&qr)[U * NO], const T (&qi)[U * NO],
+                                             T gAr, T gAi, T gBr, T gBi, T wt, T (&s1)[NR > 0 ? NR : 1],
+                                             T (&s2)[NR > 0 ? NR : 1]) const {
+    if constexpr (NB > 0) {
+      T Zr[NB], Zi[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) Zr[b] = Zi[b] = 0;
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        T Wr = 0, Wi = 0;
+        const Quad<T> C = bc.cab[j];
+        cmac(Wr, Wi, gAr, gAi, C.x, C.y);
+        cmac(Wr, Wi, gBr, gBi, C.z, C.w);
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          const int t = j * NO + o;
+          const int b0 = S::tb0(t), b1 = S::tb1(t);
+          if (b0 < 0 && b1 < 0) continue;
+          const T zr = fma(Wr, qr[t], -Wi * qi[t]), zi = fma(Wr, qi[t], Wi * qr[t]);
+          if (b0 >= 0) {
+            Zr[b0] += zr;
+            Zi[b0] += zi;
+          }
+          if (b1 >= 0) {
+            Zr[b1] += zr;
+            Zi[b1] += zi;
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int r = S::bres(b);
+        const T Hr = fma(Zr[b], bwr[b], -Zi[b] * bwi[b]);
+        const T Hi = fma(Zr[b], bwi[b], Zi[b] * bwr[b]);
+        if (WEIGHTED) {
+          s1[r] = fma(wt, Hr, s1[r]);
+          s2[r] = fma(wt * xs[b], Hi, s2[r]);
+        } else {
+          s1[r] += Hr;
+          s2[r] = fma(xs[b], Hi, s2[r]);
+        }
+      }
+    }
+  }
+
   // LO: also add the low parts of the coefficients (fp32 data events, whose
   // ln B enters the likelihood one by one).
   template <bool LO = false>

@@ -772,8 +772,12 @@ __global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_b
           const T* sbase = reinterpret_cast<const T*>(stage);
           const SmemSrc<P, S, TE> src{sbase, tid, false};
           EventCore<P, S> ev;
+          // fp32 with the gradient, up to 8 components: keep the term products for backprop_q
+          constexpr bool KEEPQ = GRAD && P::kF32 && U <= 8;
+          T qr[KEEPQ ? U * S::NO : 1], qi[KEEPQ ? U * S::NO : 1];
           ev.lineshapes(src, bc);
-          ev.components(src);
+          if constexpr (KEEPQ) ev.components_q(src, qr, qi);
+          else ev.components(src);
           const T w = WEIGHTED ? reinterpret_cast<const T*>(stage + NPL * TE * ES)[tid] : T(1);
           sw += w;
           int kr = 0, ki = 0;
@@ -803,7 +807,8 @@ __global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_b
             const T uAi = -M.x * Ai + M.z * Bi + M.w * Br;
             const T uBr = M.y * Br - M.z * Ar - M.w * Ai;
             const T uBi = -M.y * Bi + M.z * Ai - M.w * Ar;
-            ev.template backprop_lineshapes<WEIGHTED>(src, bc, uAr, uAi, uBr, uBi, w, s1, s2);
+            if constexpr (KEEPQ) ev.template backprop_q<WEIGHTED>(bc, qr, qi, uAr, uAi, uBr, uBi, w, s1, s2);
+            else ev.template backprop_lineshapes<WEIGHTED>(src, bc, uAr, uAi, uBr, uBi, w, s1, s2);
           }
         }
         release();
@@ -1002,10 +1007,15 @@ __global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_b
           const SmemSrc<P, S, TE> src{sbase, tid, false};
           EventCore<P, S> ev;
           constexpr bool RECOMPUTE = RATES && FULL && P::kF32;
+          // fp32 full evaluation with the gradient, up to 8 components: keep the
+          // term products for backprop_q
+          constexpr bool KEEPQ = FULL && GRAD && P::kF32 && !RECOMPUTE && U <= 8;
           T sc[RECOMPUTE ? U : 1];
+          T qr[KEEPQ ? U * S::NO : 1], qi[KEEPQ ? U * S::NO : 1];
           if constexpr (FULL) {
             ev.lineshapes(src, bc);
-            ev.template components<RECOMPUTE>(src, sc);
+            if constexpr (KEEPQ) ev.components_q(src, qr, qi);
+            else ev.template components<RECOMPUTE>(src, sc);
             T* cache = reinterpret_cast<T*>(static_cast<unsigned char*>(dd.cache) + tile * dd.cache_tile_bytes);
 #pragma unroll
             for (int j = 0; j < U; ++j) {
@@ -1044,7 +1054,8 @@ __global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_b
                 cmac(gAr[j], gAi[j], tAr, tAi, ev.ar[j], ev.ai[j]);
                 cmac(gBr[j], gBi[j], tBr, tBi, ev.ar[j], ev.ai[j]);
               }
-              if constexpr (FULL) ev.template backprop_lineshapes<false>(src, bc, tAr, tAi, tBr, tBi, T(1), s1, s2);
+              if constexpr (KEEPQ) ev.template backprop_q<false>(bc, qr, qi, tAr, tAi, tBr, tBi, T(1), s1, s2);
+              else if constexpr (FULL) ev.template backprop_lineshapes<false>(src, bc, tAr, tAi, tBr, tBi, T(1), s1, s2);
             }
           } else {
             bad += 1;
