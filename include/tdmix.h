@@ -309,7 +309,9 @@ enum {
                                {Ar, Ai, Br, Bi, t, x, y, Gamma} (8 input doubles; amplitudes rounded to
                                float, t to a double-float pair) out {ln B, e^{-Gamma t} B, ok, 0} */
   TDMIX_MATH_MIX_F64 = 12,  /* the same records through the fp64 path's Eq. (mix), for comparison */
-  TDMIX_MATH_CODES = 13
+  TDMIX_MATH_RCP_APPROX_F32 = 13, /* 1/v in single precision by the hardware approximation alone (the
+                                     lineshapes' reciprocal on the fp32 path) */
+  TDMIX_MATH_CODES = 14
 };
 int tdmix_test_math(int which, int64_t n, const double* in, double* out);
 

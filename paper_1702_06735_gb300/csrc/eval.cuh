@@ -59,6 +59,21 @@ __device__ __forceinline__ float rcp<float>(float v) {
   return fmaf(r, e, r);
 }
 
+// The reciprocal of a lineshape's denominator: in fp32 the hardware
+// approximation alone (rcp.approx.ftz.f32, within one ulp of the correctly
+// rounded reciprocal for positive normal v, measured by tdmix_test_math), in
+// fp64 rcp<double> (the approximation is ~2^-23 there).
+template <class T>
+__device__ __forceinline__ T rcp_lineshape(T v) {
+  if constexpr (sizeof(T) == 4) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+  } else {
+    return rcp<double>(v);
+  }
+}
+
 // Four values read together (one 128-bit shared load in fp32, two in fp64).
 template <class T>
 struct alignas(4 * sizeof(T)) Quad {
@@ -225,7 +240,7 @@ struct EventCore {
       T im;
       if constexpr (P::kF32) im = fma(R.z, X, R.w * X);
       else im = R.z * X;
-      T inv = rcp<T>(fma(delta, delta, im * im));
+      T inv = rcp_lineshape<T>(fma(delta, delta, im * im));
       bwr[b] = delta * inv;
       bwi[b] = im * inv;
       xs[b] = X;

@@ -98,6 +98,7 @@ __global__ void k_test_math(int which, int64_t n, const double* __restrict__ in,
     case TDMIX_MATH_DIV_F64: out[i] = 1.0 / v; break;
     case TDMIX_MATH_RCP_F32: out[i] = double(rcp<float>(float(v))); break;
     case TDMIX_MATH_DIV_F32: out[i] = double(1.0f / float(v)); break;
+    case TDMIX_MATH_RCP_APPROX_F32: out[i] = double(rcp_lineshape<float>(float(v))); break;
     case TDMIX_MATH_DF_RCP: {
       const float hi = float(v);
       out[i] = df_to_double(df_rcp(DF{hi, float(v - double(hi))}));

@@ -97,7 +97,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 
 MATH_CODES = {"log_table": 0, "log_cuda": 1, "rcp_f64": 2, "div_f64": 3, "rcp_f32": 4, "div_f32": 5,
               "df_rcp": 6, "mix_tier0": 7, "mix_tier1": 8, "mix_tier2": 9, "log_df": 10, "eqmix_df": 11,
-              "eqmix_f64": 12}
+              "eqmix_f64": 12, "rcp_approx_f32": 13}
 
 
 def test_philox(counter, key):
