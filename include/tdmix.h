@@ -388,6 +388,18 @@ int tdmix_server_wait(tdmix_server* s, uint64_t ticket, double* nll, double* gra
  * (completed requests per second between the first submit and the last
  * completion) since creation or the last reset. */
 int tdmix_server_stats(tdmix_server* s, double* p50_us, double* p99_us, double* evals_per_s);
+/* Latency populations of tdmix_server_latency. */
+enum tdmix_latency_kind {
+  TDMIX_LATENCY_ALL = 0,      /* every completed request (as tdmix_server_stats) */
+  TDMIX_LATENCY_RESIDENT = 1, /* requests whose sample was resident when submitted */
+  TDMIX_LATENCY_ADMITTED = 2  /* requests that waited for their sample's admission
+                               * (upload or generation, component cache) */
+};
+/* Latency percentiles (submit to completion, microseconds) of one
+ * population since creation or the last reset, and its size in *count
+ * (each output may be NULL).  An empty population gives NaN percentiles
+ * and TDMIX_OK; a kind outside tdmix_latency_kind gives TDMIX_ERR_ARG. */
+int tdmix_server_latency(tdmix_server* s, int kind, double* p50_us, double* p99_us, int64_t* count);
 int tdmix_server_reset_stats(tdmix_server* s);
 /* Device memory currently held by resident samples. */
 int tdmix_server_resident_bytes(tdmix_server* s, size_t* bytes);

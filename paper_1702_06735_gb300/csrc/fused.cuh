@@ -413,6 +413,26 @@ struct Layout {
   }
 };
 
+// The cached fp32 data pass with the gradient (and the serving kernel's)
+// forms A and Abar with the coefficients rounded to fp32, c_hi = fl32(c),
+// and leaves out the residues dc = c - c_hi (below 2^-24 |c|).  Since it
+// also sums the holomorphic sensitivities gA_j = sum_e (d ln B_e / dA)
+// a_j(e) and gB_j (the coefficient gradient), the residues enter the sum
+// of ln B to first order in the finish instead of once per event:
+//   sum ln B(c) = sum ln B(c_hi) + 2 Re sum_j (gA_j dcA_j + gB_j dcB_j) + O(|dc|^2),
+// the neglected term about 2^-48 relative.  ds holds [sum ln B, n_bad,
+// d/dx, d/dy, Re gA, Im gA, Re gB, Im gB, ...].  Component j's share (0 for
+// j >= U); the finish sums the shares over the lanes of a warp, since
+// double-precision conversions and arithmetic in one dependent chain would
+// take microseconds on this GPU.
+template <int U>
+__device__ inline double coef_residue_term(const CtaConst& cc, const double* ds, int j) {
+  if (j >= U) return 0.0;
+  const double ar = cc.cA[j][0] - double(float(cc.cA[j][0])), ai = cc.cA[j][1] - double(float(cc.cA[j][1]));
+  const double br = cc.cB[j][0] - double(float(cc.cB[j][0])), bi = cc.cB[j][1] - double(float(cc.cB[j][1]));
+  return 2.0 * ((ds[4 + j] * ar - ds[4 + U + j] * ai) + (ds[4 + 2 * U + j] * br - ds[4 + 3 * U + j] * bi));
+}
+
 // Likelihood from the MC column totals `mcs` and the data column totals
 // `ds` of one sample: writes [nll, N, n_bad or status, sum ln B,
 // n recomputed, grad...]
@@ -431,7 +451,9 @@ struct Layout {
 // warps 1-7 form the gradient.  Used by the
 // last block of an evaluation and, in serving, by the last chunk of each
 // request (256 threads).
-template <class S>
+// COEF_RESIDUE: the data sums were formed with the coefficients rounded to
+// fp32 (see coef_residue_term).
+template <class S, bool COEF_RESIDUE = false>
 __device__ inline void finish_likelihood(double* res, double* onll, double* og, int nc, int np, const CtaConst& cc,
                                          const double* mcs, const double* ds, double Nd, double sum_t, double inv_sw,
                                          bool want_grad, bool have_res_grad, int timed_out, const double2* logtab,
@@ -503,9 +525,11 @@ __device__ inline void finish_likelihood(double* res, double* onll, double* og, 
   const double AA = sh[0], BB = sh[1], Xr = sh[2], Xi = sh[3];
   const double nbar = (al * AA + be * BB - 2.0 * gc * Xr - 2.0 * dc * Xi) * inv_sw;
   if (warp == 0) {  // the logarithm; warp 0 takes no part in the gradient
+    double cres = 0.0;  // lane 0: the coefficient residue term, one component per lane
+    if constexpr (COEF_RESIDUE) cres = warp_sum(coef_residue_term<U>(cc, ds, lane));
     if (tid == 0) {
       const double N = nbar * cc.tau;
-      const double sum_lnb = ds[0], nbad = ds[1];
+      const double sum_lnb = ds[0] + cres, nbad = ds[1];
       double nll = -sum_lnb + gamma * sum_t + Nd * log_table(N, logtab);
       if (nbad > 0 || !(N > 0)) nll = nan("");
       res[0] = nll;
@@ -625,6 +649,11 @@ __global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_b
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
+  // the cached fp32 pass with the gradient forms A, Abar with the fp32
+  // coefficients and adds their rounding residues in the finish
+  // (coef_residue_term); the full pass, where the data tiles are a small
+  // share of the work, applies them per event
+  constexpr bool CRES = P::kF32 && GRAD && !FULL;
   // The next evaluation of a batch may start its blocks as this one's blocks exit.
   // The cached path reads the component cache and the stored MC totals that
   // the evaluation before it wrote, so it waits for that one first.
@@ -1030,7 +1059,7 @@ __global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_b
             }
           }
           T Ar_, Ai_, Br_, Bi_;
-          ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
+          ev.template amplitudes<!CRES>(bc, Ar_, Ai_, Br_, Bi_);
           T tAr, tAi, tBr, tBi;
           bool ok_ev;
           if constexpr (P::kF32) {
@@ -1219,7 +1248,7 @@ __global__ void __launch_bounds__(kTile, FULL ? 1 : Layout<P, S, GRAM>::cached_b
   }
   if (trace && tid == 0) trace[5] = global_ns();
   if (tid == 0) *a.counter = 0u;
-  finish_likelihood<S>(a.result, a.out_nll, a.out_grad, a.km.n_chains, a.km.n_params, cc, colsum, colsum + WMC,
+  finish_likelihood<S, CRES>(a.result, a.out_nll, a.out_grad, a.km.n_chains, a.km.n_params, cc, colsum, colsum + WMC,
                        double(dd.n), a.sum_t, a.inv_sum_w, GRAD, FULL && GRAD, s_timeout != 0, logtab, trace);
   __syncthreads();
   if (trace && tid == 0) trace[7] = global_ns();

@@ -119,6 +119,7 @@ struct Request {
   int sample;
   std::vector<double> params;
   double t_submit;
+  bool admitted = false;  // its sample was not resident at submission
 };
 
 struct Done {
@@ -180,6 +181,7 @@ struct tdmix_server {
   std::vector<double> env_params;
   double env_value = 0;
   std::vector<double> latencies;
+  std::vector<double> latencies_by_kind[2];  // resident at submission, admitted for the request
   double t_first = 0, t_last = 0;
   uint64_t n_done = 0, use_clock = 0;
   std::string err;
@@ -254,6 +256,7 @@ void complete(tdmix_server* s, int slot, InFlight& inf, int status, const double
   auto it = s->samples.find(inf.req.sample);
   if (it != s->samples.end()) it->second.pending--;
   s->latencies.push_back(d.latency_s);
+  s->latencies_by_kind[inf.req.admitted ? 1 : 0].push_back(d.latency_s);
   if (s->n_done == 0) s->t_first = inf.req.t_submit;
   s->t_last = now_s();
   s->n_done++;
@@ -634,6 +637,7 @@ int tdmix_server_submit(tdmix_server* s, int sample_id, const double* params, ui
     s->ready.push_back(std::move(q));
     s->cv_dispatch.notify_all();
   } else {
+    q.admitted = true;
     s->waiting.push_back(std::move(q));
     s->cv_admit.notify_all();
   }
@@ -657,16 +661,39 @@ int tdmix_server_wait(tdmix_server* s, uint64_t ticket, double* nll, double* gra
   return TDMIX_OK;
 }
 
+namespace {
+
+// nearest-rank percentile q of the latencies l (sorted in place), microseconds
+double percentile_us(std::vector<double>& l, double q) {
+  std::sort(l.begin(), l.end());
+  return l[std::min(l.size() - 1, size_t(q * (l.size() - 1) + 0.5))] * 1e6;
+}
+
+}  // namespace
+
 int tdmix_server_stats(tdmix_server* s, double* p50_us, double* p99_us, double* evals_per_s) {
   if (!s) return TDMIX_ERR_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
   std::vector<double> l = s->latencies;
   if (l.empty()) return sfail(s, TDMIX_ERR_STATE, "no completed requests");
-  std::sort(l.begin(), l.end());
-  auto pct = [&](double q) { return l[std::min(l.size() - 1, size_t(q * (l.size() - 1) + 0.5))] * 1e6; };
-  if (p50_us) *p50_us = pct(0.50);
-  if (p99_us) *p99_us = pct(0.99);
+  if (p50_us) *p50_us = percentile_us(l, 0.50);
+  if (p99_us) *p99_us = percentile_us(l, 0.99);
   if (evals_per_s) *evals_per_s = s->t_last > s->t_first ? double(s->n_done) / (s->t_last - s->t_first) : 0.0;
+  return TDMIX_OK;
+}
+
+int tdmix_server_latency(tdmix_server* s, int kind, double* p50_us, double* p99_us, int64_t* count) {
+  if (!s || kind < TDMIX_LATENCY_ALL || kind > TDMIX_LATENCY_ADMITTED) return sfail(s, TDMIX_ERR_ARG, "bad argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::vector<double> l = kind == TDMIX_LATENCY_ALL ? s->latencies : s->latencies_by_kind[kind - 1];
+  if (count) *count = int64_t(l.size());
+  if (l.empty()) {
+    if (p50_us) *p50_us = NAN;
+    if (p99_us) *p99_us = NAN;
+    return TDMIX_OK;
+  }
+  if (p50_us) *p50_us = percentile_us(l, 0.50);
+  if (p99_us) *p99_us = percentile_us(l, 0.99);
   return TDMIX_OK;
 }
 
@@ -674,6 +701,8 @@ int tdmix_server_reset_stats(tdmix_server* s) {
   if (!s) return TDMIX_ERR_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
   s->latencies.clear();
+  s->latencies_by_kind[0].clear();
+  s->latencies_by_kind[1].clear();
   s->n_done = 0;
   s->t_first = s->t_last = 0;
   return TDMIX_OK;

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
           ev.ai[k] = sbase[(U + k) * TE + tid];
         }
         T Ar_, Ai_, Br_, Bi_;
-        ev.template amplitudes<true>(bc, Ar_, Ai_, Br_, Bi_);
+        ev.template amplitudes<!(P::kF32 && GRAD)>(bc, Ar_, Ai_, Br_, Bi_);  // see coef_residue_term
         T tAr, tAi, tBr, tBi;
         bool ok_ev;
         if constexpr (P::kF32)
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kTile, 1) k_serve_loop(const __grid_constant__
     }
     __syncthreads();
     const int timed_out = *static_cast<volatile int*>(a.status) & 1;
-    finish_likelihood<S>(a.slots[slot].result, nullptr, nullptr, nc, np, cc, colsum, colsum + WMC, double(n_ev),
+    finish_likelihood<S, P::kF32 && GRAD>(a.slots[slot].result, nullptr, nullptr, nc, np, cc, colsum, colsum + WMC, double(n_ev),
                          s_req.sum_t, a.inv_sum_w, GRAD, false, timed_out, logtab, nullptr);
     __threadfence_system();
     __syncthreads();

@@ -21,6 +21,7 @@ MODEL_DIR = os.path.join(HERE, "amplitude_models")
 FP64, FP32 = 0, 1
 GENERIC = 0x100      # flag: the runtime-table kernels whatever the structure
 KERNEL_PATHS = {0: "fp64", 1: "fp32", 2: "generic"}
+LATENCY_ALL, LATENCY_RESIDENT, LATENCY_ADMITTED = 0, 1, 2  # tdmix_latency_kind
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_STATE", -5: "ERR_NONFINITE",
           -6: "ERR_DOMAIN", -7: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
 
@@ -60,6 +61,7 @@ _SIGNATURES = {
     "tdmix_server_submit": (_c_i, [_c_p, _c_i, _c_p, ctypes.POINTER(ctypes.c_uint64)]),
     "tdmix_server_wait": (_c_i, [_c_p, ctypes.c_uint64, _c_p, _c_p, ctypes.c_double]),
     "tdmix_server_stats": (_c_i, [_c_p, _c_p, _c_p, _c_p]),
+    "tdmix_server_latency": (_c_i, [_c_p, _c_i, _c_p, _c_p, ctypes.POINTER(ctypes.c_int64)]),
     "tdmix_server_reset_stats": (_c_i, [_c_p]),
     "tdmix_server_resident_bytes": (_c_i, [_c_p, ctypes.POINTER(ctypes.c_size_t)]),
     "tdmix_server_last_error": (ctypes.c_char_p, [_c_p]),
@@ -435,9 +437,17 @@ class TDMixServer:
         return self.wait(self.submit(sample_id, params), timeout_s)
 
     def stats(self) -> dict:
+        """p50/p99 latency over all completed requests and throughput; the same
+        percentiles for requests on resident samples ("resident") and for those
+        that waited for their sample's admission ("admitted"), with counts."""
         a, b, c = np.empty(1), np.empty(1), np.empty(1)
         self._check(self._lib.tdmix_server_stats(self._s, a.ctypes.data, b.ctypes.data, c.ctypes.data))
-        return {"p50_us": float(a[0]), "p99_us": float(b[0]), "evals_per_s": float(c[0])}
+        out = {"p50_us": float(a[0]), "p99_us": float(b[0]), "evals_per_s": float(c[0])}
+        for kind, name in ((LATENCY_RESIDENT, "resident"), (LATENCY_ADMITTED, "admitted")):
+            n = ctypes.c_int64()
+            self._check(self._lib.tdmix_server_latency(self._s, kind, a.ctypes.data, b.ctypes.data, ctypes.byref(n)))
+            out[name] = {"count": int(n.value), "p50_us": float(a[0]), "p99_us": float(b[0])}
+        return out
 
     def reset_stats(self):
         self._check(self._lib.tdmix_server_reset_stats(self._s))

@@ -91,6 +91,54 @@ def test_cached_path_matches_full_path(name, nd, nm, wid):
     assert np.max(np.abs(g - g0) / S) <= 1e-12
 
 
+@pytest.mark.parametrize("name,nd,nm,wid", [("d0_k3pi_2chain", 1000, 10_000, 0), ("d0_k3pi_full", 3001, 60_001, 1)])
+def test_fp32_cached_pass_coefficient_residues(name, nd, nm, wid):
+    """The cached fp32 pass forms A and Abar with the coefficients rounded to
+    fp32 and adds the rounding residues to the sum of ln B to first order in
+    the finish.  (1) A coefficient step below fp32 resolution leaves every
+    fp32 quantity of the pass unchanged, so the NLL moves only through the
+    double-precision terms of the finish: by the gradient times the step (a
+    residue term left out, of the wrong sign or on the wrong component moves
+    it by the normalisation part alone, several times off).  (2) Against the
+    full pass on the same component values the NLL differs by the full
+    pass's fp32 rounding of A (~1e-7 per event, random) and the gradient by
+    far less than the fp32 path's own error."""
+    m, data, t, mc = workload(name, nd, nm, wid)
+    c = _ctx(name, "fp32", data, t, mc)
+    mask = m.floating_mask().numpy().astype(np.int32)
+    nc, nr = len(m.chains), len(m.resonances)
+    fixed = mask.copy()
+    fixed[2 * nc:2 * nc + 2 * nr] = 0
+    c.set_floating(fixed)
+    c.nll(m.default_params().numpy())          # full pass: fills the component cache
+    p1 = perturbed_params(m, 21, masses=False)
+    v_c, g_c = c.nll(p1)                       # cached pass
+    worst = 0.0
+    for k in [q for q in range(2 * nc) if fixed[q] and p1[q] != 0][:6]:
+        # two points inside the rounding interval of h = fl32(p1[k]): h + 0.05 s and
+        # h + 0.2 s, s the fp32 spacing at h (the interval reaches at least s / 4 on
+        # either side, also at a power of two)
+        h = float(np.float32(p1[k]))
+        s_k = abs(float(np.spacing(np.float32(h))))
+        a, b = p1.copy(), p1.copy()
+        a[k], b[k] = h + 0.05 * s_k, h + 0.2 * s_k
+        assert np.float32(a[k]) == np.float32(b[k]) == np.float32(h)
+        v_a, g_a = c.nll(a)
+        v_b, _ = c.nll(b)
+        dv, lin = v_b - v_a, g_a[k] * (b[k] - a[k])
+        worst = max(worst, abs(dv - lin) / abs(lin))
+        assert abs(dv - lin) <= 1e-3 * abs(lin) + 1e-10, (k, dv, lin)
+    c.set_floating(mask)
+    v_f, g_f = c.nll(p1)                       # full pass (masses and widths floating)
+    c.close()
+    S = grad_scale(m, data, t, mc, p1)
+    sel = fixed.astype(bool)
+    gerr = np.max(np.abs(g_c - g_f)[sel] / S[sel])
+    print(f"\n{name}: sub-ulp steps {worst:.2e} of g * step; cached - full NLL {v_c - v_f:.2e}, gradient {gerr:.2e}")
+    assert abs(v_c - v_f) <= 1e-4
+    assert gerr <= 1e-6
+
+
 def test_weighted_mc_and_ragged_tiny_samples():
     m, data, t, mc = workload("d0_k3pi_2chain", 1000, 10_000, 0)
     w = np.random.default_rng(4).uniform(0.5, 2.0, 257)

@@ -147,6 +147,19 @@ def test_concurrent_minimisers_and_stats():
     assert not errors, errors
     st = s.stats()
     assert st["p50_us"] > 0 and st["p99_us"] >= st["p50_us"] and st["evals_per_s"] > 0
+    # the first request of each sample waited for its admission, the other
+    # 14 found it resident (1 GiB holds all eight)
+    assert st["admitted"]["count"] == 8 and st["resident"]["count"] == 8 * 14
+    assert st["admitted"]["p50_us"] > st["resident"]["p50_us"] > 0
+    # after a reset every population is empty: NaN percentiles, count 0
+    import ctypes
+    from paper_1702_06735_gb300.tdmix import LATENCY_ADMITTED
+    s.reset_stats()
+    n = ctypes.c_int64(-1)
+    a, b = np.empty(1), np.empty(1)
+    assert s._lib.tdmix_server_latency(s._s, LATENCY_ADMITTED, a.ctypes.data, b.ctypes.data, ctypes.byref(n)) == 0
+    assert n.value == 0 and np.isnan(a[0]) and np.isnan(b[0])
+    assert s._lib.tdmix_server_latency(s._s, 3, None, None, None) == -1
     s.close()
 
 
