@@ -10,18 +10,27 @@ that submits NLL + gradient requests to the device-resident loop, and,
 optionally, its x, y errors come from the Hessian of the NLL at the minimum
 (central differences of the analytic gradient).  Host orchestration only:
 every likelihood, gradient and event comes from the GPU.
+
+Both studies can keep a checkpoint (ToyCheckpoint): every finished toy is
+appended to a file as it ends, and a study started again with the same
+file and the same arguments fits only the toys the file does not hold.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import dataclasses
+import hashlib
+import json
 import math
+import os
+import threading
 import time
 from dataclasses import dataclass
 
 import numpy as np
 
 from . import minimize
-from .tdmix import TDMixError, TDMixServer
+from .tdmix import TDMixError, TDMixServer, model_json
 
 
 @dataclass
@@ -33,6 +42,85 @@ class ToyFit:
     sy: float
     converged: bool
     n_eval: int
+
+
+class ToyCheckpoint:
+    """Checkpoint of a toy study: a JSON-lines file whose first line holds
+    the study's fingerprint (model, sizes, generating parameters, seeds, MC
+    sample digest, fit settings) and whose further lines are finished toys,
+    {"toy": index, ...}, each appended, flushed and synced to disk when its
+    fit ends.  Opening an existing file with the same fingerprint gives its
+    records (`records`: index -> record) and appends to it; a different
+    fingerprint raises ValueError, and so does a complete line that does not
+    parse.  Text after the last newline (a line cut short when the process
+    stopped) is dropped from the file.  record() may be called from several
+    threads."""
+
+    def __init__(self, path, fingerprint: dict):
+        self.path = os.fspath(path)
+        self.records: dict[int, dict] = {}
+        self._lock = threading.Lock()
+        head = json.dumps({"checkpoint": fingerprint}, sort_keys=True)
+        keep, size = 0, 0
+        if os.path.exists(self.path):
+            with open(self.path, "rb") as f:
+                raw = f.read()
+            size = len(raw)
+            complete = raw.split(b"\n")[:-1]  # lines that end with a newline
+            if complete:
+                try:
+                    found = json.loads(complete[0])
+                except ValueError:
+                    raise ValueError(f"{self.path} is not a toy-study checkpoint") from None
+                if found != json.loads(head):
+                    raise ValueError(f"{self.path} is the checkpoint of a different study")
+                keep = len(complete[0]) + 1
+                for n, line in enumerate(complete[1:], start=2):
+                    try:
+                        rec = json.loads(line)
+                        k = int(rec["toy"])
+                    except (ValueError, KeyError, TypeError):
+                        raise ValueError(f"{self.path}: line {n} is not a toy record") from None
+                    self.records[k] = rec
+                    keep += len(line) + 1
+        if keep == 0:  # new file, or not even the fingerprint line was complete
+            with open(self.path, "wb") as f:
+                f.write(head.encode() + b"\n")
+                f.flush()
+                os.fsync(f.fileno())
+        elif keep < size:
+            with open(self.path, "r+b") as f:
+                f.truncate(keep)
+        self._f = open(self.path, "ab")
+
+    def record(self, toy: int, **fields):
+        line = json.dumps({"toy": int(toy), **fields}).encode() + b"\n"
+        with self._lock:
+            self._f.write(line)
+            self._f.flush()
+            os.fsync(self._f.fileno())
+
+    def close(self):
+        with self._lock:
+            if not self._f.closed:
+                self._f.close()
+
+
+def _digest(a) -> str:
+    """sha256 of an array's float64 values (host or device tensor, or array)."""
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return hashlib.sha256(str(a.shape).encode() + a.tobytes()).hexdigest()
+
+
+def _fingerprint(study: str, model, precision, sizes, gen_params, mc, seed, stream0, **settings) -> dict:
+    out = {"study": study, "model": json.loads(model_json(model)), "precision": precision,
+           "sizes": [int(n) for n in sizes], "gen_params": [float(v) for v in np.asarray(gen_params).ravel()],
+           "mc_sha256": _digest(mc), "seed": int(seed), "stream0": int(stream0)}
+    for k, v in settings.items():
+        out[k] = None if v is None else (np.asarray(v).tolist() if isinstance(v, (np.ndarray, list, tuple)) else v)
+    return out
 
 
 def _objective(srv, sid):
@@ -47,20 +135,35 @@ def _objective(srv, sid):
 
 
 def run(model, precision: str, sizes, gen_params, mc, seed: int, stream0: int = 1000, clients: int = 16,
-        budget_bytes: int = 4 << 30, with_errors: bool = False, start_shift: float = 1e-3):
+        budget_bytes: int = 4 << 30, with_errors: bool = False, start_shift: float = 1e-3, checkpoint=None):
     """Generate len(sizes) toys of the given sizes at gen_params, fit x and y
     of each (the model and the coefficients fixed) and return
-    (list of ToyFit, server statistics dict)."""
+    (list of ToyFit, server statistics dict).  With `checkpoint` (a path),
+    finished toys are kept in a ToyCheckpoint and the toys it already holds
+    are not fitted again (statistics["resumed"] counts them; the server
+    statistics cover this call's fits).  A resumed toy is generated from the
+    same seed and stream, but the server finds the generator's envelope again
+    at its first admission, so its events are an equally valid draw of the
+    model rather than the same ones."""
     gen_params = np.asarray(gen_params, dtype=np.float64)
+    cp = None
+    if checkpoint is not None:
+        cp = ToyCheckpoint(checkpoint, _fingerprint("fixed-model toys", model, precision, sizes, gen_params, mc, seed,
+                                                    stream0, with_errors=with_errors, start_shift=start_shift))
     srv = TDMixServer(model, precision, hbm_budget_bytes=budget_bytes, max_slots=256)
     try:
         srv.add_mc(mc)
-        ids = [srv.add_generated_sample(gen_params, int(n), seed, stream0 + k) for k, n in enumerate(sizes)]
+        fits = [None] * len(sizes)
+        if cp is not None:
+            for k, rec in cp.records.items():
+                if 0 <= k < len(sizes):
+                    fits[k] = ToyFit(**rec["fit"])
+        todo = [k for k in range(len(sizes)) if fits[k] is None]
+        ids = {k: srv.add_generated_sample(gen_params, int(sizes[k]), seed, stream0 + k) for k in todo}
         mask = np.zeros(len(gen_params), dtype=bool)
         mask[-2:] = True
         scale = np.ones(len(gen_params))
         scale[-2:] = 1e-3
-        fits = [None] * len(sizes)
 
         def fit(k):
             fg = _objective(srv, ids[k])
@@ -75,18 +178,23 @@ def run(model, precision: str, sizes, gen_params, mc, seed: int, stream0: int = 
                 sx, sy = float(err[-2]), float(err[-1])
                 n_eval += 4
             fits[k] = ToyFit(int(sizes[k]), float(r.x[-2]), float(r.x[-1]), sx, sy, bool(r.converged), int(n_eval))
+            if cp is not None:
+                cp.record(k, fit=dataclasses.asdict(fits[k]))
 
         srv.reset_stats()
         t0 = time.perf_counter()
         with cf.ThreadPoolExecutor(max_workers=clients) as ex:
-            list(ex.map(fit, range(len(sizes))))
+            list(ex.map(fit, todo))
         wall = time.perf_counter() - t0
-        st = srv.stats()
+        st = srv.stats() if todo else {}
         st.update(srv.loop_info())
         st["wall_s"] = wall
+        st["resumed"] = len(sizes) - len(todo)
         return fits, st
     finally:
         srv.close()
+        if cp is not None:
+            cp.close()
 
 
 @dataclass
@@ -100,7 +208,7 @@ class FloatingFit:
 
 
 def run_floating(model, precision: str, sizes, gen_params, mc, seed: int, stream0: int = 1000, floating=None,
-                 start_shift: float = 1e-3, scale=None, compare_fixed: bool = False):
+                 start_shift: float = 1e-3, scale=None, compare_fixed: bool = False, checkpoint=None):
     """Pseudo-experiments fitted with the model floating: every parameter of
     the `floating` mask (default: every resonance mass and width with x and
     y; the chain coefficients stay at their generating values, since a
@@ -114,9 +222,17 @@ def run_floating(model, precision: str, sizes, gen_params, mc, seed: int, stream
     Errors from the Hessian over all floating parameters.  With
     compare_fixed, the same events are also fitted with the model fixed (x, y
     floating), whose errors are the conditional ones.  Returns a list of
-    FloatingFit."""
+    FloatingFit.  With `checkpoint` (a path), finished toys are kept in a
+    ToyCheckpoint with the generator's envelope, and a study started again
+    takes the toys it holds from it and generates the others with the same
+    envelope: the same events and fits as an uninterrupted study."""
     from .tdmix import TDMix
     gen_params = np.asarray(gen_params, dtype=np.float64)
+    cp = None
+    if checkpoint is not None:
+        cp = ToyCheckpoint(checkpoint, _fingerprint("floating-model toys", model, precision, sizes, gen_params, mc,
+                                                    seed, stream0, floating=floating, start_shift=start_shift,
+                                                    scale=scale, compare_fixed=compare_fixed))
     c = TDMix(model, precision)
     try:
         if floating is None:
@@ -132,7 +248,18 @@ def run_floating(model, precision: str, sizes, gen_params, mc, seed: int, stream
         c.load_events(mc_p4=mc)
         out = []
         env = 0.0  # the generator's envelope, found by the first toy and reused (same parameters)
+        done = {}
+        if cp is not None:
+            for k, rec in cp.records.items():
+                d = dict(rec["fit"])
+                done[k] = FloatingFit(int(d["n_events"]), np.asarray(d["params"], dtype=np.float64),
+                                      np.asarray(d["errors"], dtype=np.float64), bool(d["converged"]),
+                                      int(d["n_eval"]), tuple(d["xy_fixed_model"]))
+                env = float(rec["envelope"])
         for k, n in enumerate(sizes):
+            if k in done:
+                out.append(done[k])
+                continue
             p4, t, info = c.generate(int(n), seed=seed, stream=stream0 + k, params=gen_params, envelope=env)
             env = info["envelope"]
             c.load_events(p4, t)
@@ -153,9 +280,15 @@ def run_floating(model, precision: str, sizes, gen_params, mc, seed: int, stream
                 fit.xy_fixed_model = (float(rf.x[-2]), float(rf.x[-1]), float(ef[-2]), float(ef[-1]))
                 c.set_floating(mask.astype(np.int32))
             out.append(fit)
+            if cp is not None:
+                cp.record(k, envelope=env, fit={"n_events": fit.n_events, "params": fit.params.tolist(),
+                                                "errors": np.asarray(fit.errors).tolist(), "converged": fit.converged,
+                                                "n_eval": fit.n_eval, "xy_fixed_model": list(fit.xy_fixed_model)})
         return out
     finally:
         c.close()
+        if cp is not None:
+            cp.close()
 
 
 def _model_dict(model) -> dict:
