@@ -11,7 +11,8 @@ hand-written adjoint on the GPU.
 
 Parity status per function (what pins it is in tests/test_oracle_*.py):
   breit_wigner, mass_dependent_width, blatt_weisskopf ... pinned (pole closed
-      form, width at the pole, barrier limits)
+      form, width at the pole and off it from the two-body phase space and
+      barrier ratio written out, values below threshold, barrier limits)
   spin factors ........................................... pinned (Lorentz
       invariance, rest-frame closed forms on constructed events, edge zeros)
   chain amplitudes / Bose symmetrisation ................. pinned (exchange
@@ -21,6 +22,12 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
   time integrals / normalisation ......................... pinned (quadrature)
   NLL and its gradient ................................... pinned (hand-computed
       one-chain case, central finite differences)
+  rate_resolved (decay-time resolution, an extension) .... pinned (closed-form
+      folds through the Faddeeva function, the erfcx case x = y = 0, the
+      narrow-resolution limit, the time integral over the real line)
+  background_density and the mixture NLL (an extension) .. pinned (integral
+      one, pure-background closed form, the no-background limit, central
+      finite differences)
   the absolute value of the NLL for the D0 -> K3pi model .. parity unpinned:
       the paper prints no worked example, model or fit values.
 """
