@@ -832,7 +832,7 @@ def toy_study(precision, sizes, mc, p0, label):
             "loop": {k: st[k] for k in ("launches", "abnormal_exits", "published", "last_exit_status")}}
 
 
-def serving_throughput(mc, p0, precision="fp32", n_samples=64, n_events=100_000, rounds=40, clients=16,
+def serving_throughput(mc, p0, precision="fp32", n_samples=64, n_events=100_000, rounds=160, clients=16,
                        per_client=4):
     """The device-resident serving loop at steady state: n_samples generated
     samples of n_events (model fixed) are made resident by one request each,
