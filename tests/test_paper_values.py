@@ -1,0 +1,43 @@
+"""The paper's printed numbers kept in tests/golden/paper_values.json,
+checked against what the mathematics fixes about them (a mistyped entry
+fails here).
+
+Table 1 (Sec. 4): the statistical sensitivities to x and y at 20k, 50k and
+70k events come from toy fits, so they scale as 1/sqrt(N).  The x column
+does so within the rounding of its printed digits; the y column within the
+statistical precision of a spread estimated from toys (its 70k entry is one
+unit of the last digit above the scaled 50k value)."""
+import json
+import math
+
+from conftest import GOLDEN_DIR
+
+
+def _gold():
+    with open(f"{GOLDEN_DIR}/paper_values.json") as f:
+        return json.load(f)
+
+
+def test_table1_x_column_scales_as_one_over_sqrt_n_within_rounding():
+    t = _gold()["sensitivity"]
+    half_unit = 0.0005  # the entries are printed to three decimals (percent)
+    lo = max((s - half_unit) * math.sqrt(n) for s, n in zip(t["sigma_x_percent"], t["events"]))
+    hi = min((s + half_unit) * math.sqrt(n) for s, n in zip(t["sigma_x_percent"], t["events"]))
+    assert lo <= hi, (lo, hi)  # one sigma * sqrt(N) reproduces every printed entry
+
+
+def test_table1_y_column_scales_as_one_over_sqrt_n_within_toy_precision():
+    t = _gold()["sensitivity"]
+    v = [s * math.sqrt(n) for s, n in zip(t["sigma_y_percent"], t["events"])]
+    mean = sum(v) / len(v)
+    assert max(abs(a / mean - 1) for a in v) <= 0.05
+    # and the two columns agree in size, as for comparable x and y sensitivity
+    vx = [s * math.sqrt(n) for s, n in zip(t["sigma_x_percent"], t["events"])]
+    assert abs(mean / (sum(vx) / len(vx)) - 1) <= 0.1
+
+
+def test_table1_sizes_and_mixing_inputs():
+    g = _gold()
+    assert g["sensitivity"]["events"] == [20000, 50000, 70000]
+    # the world averages the toys are generated at (abstract, Table 1 caption)
+    assert (g["mixing_inputs"]["x"], g["mixing_inputs"]["y"]) == (0.0049, 0.0061)
