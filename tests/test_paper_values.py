@@ -41,3 +41,37 @@ def test_table1_sizes_and_mixing_inputs():
     assert g["sensitivity"]["events"] == [20000, 50000, 70000]
     # the world averages the toys are generated at (abstract, Table 1 caption)
     assert (g["mixing_inputs"]["x"], g["mixing_inputs"]["y"]) == (0.0049, 0.0061)
+
+
+def _linear_fit_max_rel_residual(x, y):
+    n = len(x)
+    mx, my = sum(x) / n, sum(y) / n
+    b = sum((a - mx) * (c - my) for a, c in zip(x, y)) / sum((a - mx) ** 2 for a in x)
+    a0 = my - b * mx
+    return max(abs(a0 + b * u - v) / v for u, v in zip(x, y)), b
+
+
+def test_table3_fit_time_is_linear_in_the_normalisation_points():
+    """Sec. 5 states the fit time grows linearly with the number of
+    normalisation points; every column of Table 3 follows a straight line in
+    them (within 10 %; 15 % for the 48-thread column, which bends with
+    hyper-threading) with a positive slope, and the K40 is the fastest at
+    every size."""
+    t = _gold()["fit_time_seconds"]
+    x = [v / 1e6 for v in t["norm_points"]]
+    for col, tol in (("xeon_24_cores", 0.10), ("xeon_48_threads", 0.15), ("k40", 0.10)):
+        r, slope = _linear_fit_max_rel_residual(x, t[col])
+        assert r <= tol and slope > 0, (col, r, slope)
+    for k in range(len(x)):
+        assert t["k40"][k] < t["xeon_48_threads"][k] < t["xeon_24_cores"][k]
+
+
+def test_table2_generation_time_is_proportional_to_the_events():
+    """Table 2: accept/reject generation time per event is the same at 20k,
+    50k and 70k events within 10 % on each platform, and the K40 is faster."""
+    t = _gold()["generation_time_seconds"]
+    for col in ("xeon_24_cores", "k40"):
+        per = [s / n for s, n in zip(t[col], t["events"])]
+        m = sum(per) / len(per)
+        assert max(abs(p / m - 1) for p in per) <= 0.10, (col, per)
+    assert all(g < c for g, c in zip(t["k40"], t["xeon_24_cores"]))
